@@ -1,0 +1,290 @@
+#!/usr/bin/env python
+"""Benchmark of the full ion-flow-around-dust step on GB300.
+
+One "step" is one pass of the whole method over the ion population: push + absorption
++ outflow + compaction + re-injection, all-pairs forces, kick + collisions, grain
+update.  The metric is ordered ion pair-interactions per second, N (N - 1) per step
+(the O(N^2) work of Sec. 5), over the whole job; ion-steps/s is reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun) every rank runs an independent replica with its own seed (the
+method's runs do not exchange data): weak scaling, max time over ranks.
+--impl reference times the FP64 CPU oracle (the only reference implementation) on the
+host cores, each step a bounded sample of the same workload's pair forces.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2205_06557_gb300 import workloads as W  # noqa: E402
+
+METRIC = "ion pair-interactions/s"
+UNIT = "pairs/s"
+PAIRS_PER_CLK_SM = 8.0  # FP32 pipe (16 FP32 ops / pair at 128 lanes) and SFU (2 MUFU / pair at 16 lanes)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="scale", choices=["scale", "tiny", "chain"])
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(name, seed):
+    if name == "tiny":
+        return W.tiny(seed=seed), "ion flow past one 20 um grain, ~2,000 ions (R=0.2 mm, H=0.4 mm)"
+    if name == "chain":
+        return W.dust_chain(n_dust=4, seed=seed), "4-grain chain along the flow, ~1,000,000 ions (R=1 mm, H=8 mm)"
+    return W.at_scale(seed=seed), "ion flow past one 20 um grain, ~200,000 ions (R=0.9267 mm, H=1.853 mm)"
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region"""
+
+    FIELDS = "pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active," \
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown," \
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, bus_id):
+        self.bus = (bus_id or "").lower()
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        rows = [[c.strip() for c in r] for r in rows if len(r) >= 9]
+        mine = [r for r in rows if self.bus and self.bus.endswith(r[0].lower()[-12:])] or rows
+        sm = [float(r[1]) for r in mine if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in mine if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for r in mine for j in range(4) if r[5 + j].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(sm)}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def cpu_baseline(p, seconds):
+    """the FP64 oracle's pair forces for a sample of target ions against all ions"""
+    import oracle
+
+    o = oracle.Oracle(dict(p, n_ions=1))
+    n = int(round(p["n_inf"] * math.pi * p["R"] ** 2 * p["H"] / p.get("weight", 1.0)))
+    x, v, ids = W.random_ions(n, p["R"], p["H"], seed=12345, dust=p["dust"])
+    o.load_ions(x, v, ids)
+    t0 = time.perf_counter()
+    m0 = min(64, n)
+    o.forces(0, m0, dust=False)
+    rate = m0 / max(time.perf_counter() - t0, 1e-6)
+    m = int(max(m0, min(n, rate * seconds)))
+    t0 = time.perf_counter()
+    o.forces(0, m, dust=False)
+    dt = time.perf_counter() - t0
+    return {"value": m * (n - 1) / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "FP64 oracle pair forces of %d of %d target ions against all %d ions (%.1f s)" % (m, n, n, dt)}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    p, desc = workload(args.workload, 0)
+    import oracle
+
+    o = oracle.Oracle(dict(p, n_ions=1))
+    n = int(round(p["n_inf"] * math.pi * p["R"] ** 2 * p["H"] / p.get("weight", 1.0)))
+    x, v, ids = W.random_ions(n, p["R"], p["H"], seed=12345, dust=p["dust"])
+    o.load_ions(x, v, ids)
+    t0 = time.perf_counter()
+    o.forces(0, 64, dust=False)
+    rate = 64 / (time.perf_counter() - t0)
+    m = int(max(64, min(n, rate * 120.0 / max(args.steps + args.warmup, 1))))
+    for s in range(args.warmup):
+        o.forces((s * m) % n, min(n, (s * m) % n + m), dust=False)
+    t0 = time.perf_counter()
+    done = 0
+    for s in range(args.steps):
+        i0 = (s * m) % max(n - m, 1)
+        o.forces(i0, i0 + m, dust=False)
+        done += m
+    dt = time.perf_counter() - t0
+    val = done * (n - 1) / dt
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": desc, "n_ions": n},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": "each step: FP64 oracle pair forces of %d target ions against all %d ions"
+                                       % (m, n)},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+
+    import paper_2205_06557_gb300 as od
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    p, desc = workload(args.workload, rank)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)  # library, flush writes and timing events share this stream
+    run = od.Run(p, stream=ctypes_stream(stream))
+    N = run.N
+    info = run.info()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        run.step(1)
+    od.od_set_profiling(run.h, 1)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    bus = getattr(torch.cuda.get_device_properties(local), "pci_bus_id", None)
+    clocks = Clocks(bus)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        run.step(1)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    t_ms = sum(a.elapsed_time(b) for a, b in ev)
+    kms, kn = od.od_kernel_times(run.h)
+    od.od_set_profiling(run.h, 0)
+    tt = torch.tensor([t_ms], dtype=torch.float64, device="cuda")
+    units = torch.tensor([float(N) * (N - 1) * args.steps], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        dist.all_reduce(units, op=dist.ReduceOp.SUM)
+    t_max = float(tt.item())
+    pairs = float(units.item())
+    value = pairs / (t_max / 1e3)
+
+    # end to end through the ABI with host buffers: upload state, one step, read back
+    x, v, a, ids = run.get_ions()
+    pin = lambda arr: torch.from_numpy(np.ascontiguousarray(arr)).pin_memory().numpy()
+    hx, hv, ha, hid = pin(x), pin(v), pin(a), pin(ids)
+    nid = int(run.counters()[15])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        run.set_ions(hx, hv, hid, nid, a=ha)
+        run.step(1)
+        hx, hv, ha, hid = run.get_ions()
+        nid = int(run.counters()[15])
+        run.dust_state()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    e2e_units = float(N) * (N - 1) * world
+    h2d = N * (3 * 8 + 3 * 8 + 3 * 8 + 8)
+    d2h = N * (3 * 8 + 3 * 8 + 3 * 8 + 8) + run.D * 4 * 8 + 16 * 8
+
+    if rank != 0:
+        run.close()
+        if dist:
+            dist.destroy_process_group()
+        return
+    pk = peaks()
+    sms = int(info["sms"])
+    clk_max = float(pk.get("sm_max_mhz") or clk.get("sm_max_mhz") or 2070.0)
+    peak = sms * clk_max * 1e6 * PAIRS_PER_CLK_SM
+    k1_ms = kms[1] / max(kn[1], 1)
+    k1_rate = float(N) * (N - 1) / (k1_ms / 1e3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": desc, "n_ions": N, "n_dust": run.D, "steps_timed": args.steps,
+                   "l2": "flushed between timed steps (256 MB write)", "parallelism": "replicas" if world > 1 else "1 GPU",
+                   "precision": "pair forces FP32; ion state, grain sums and averages FP64"},
+        "ion_steps_per_s": world * float(N) * args.steps / (t_max / 1e3),
+        "wall_s_timed": wall,
+        "kernel_ms_per_step": {"push_scan_inject": kms[0] / max(kn[0], 1), "pair_forces": k1_ms,
+                               "kick_collide": kms[2] / max(kn[2], 1), "grain_update": kms[3] / max(kn[3], 1)},
+        "roofline": {"bound": "alu", "kernel": "k_forces", "achieved": k1_rate / 1e9, "peak": peak / 1e9,
+                     "unit": "Gpair/s", "frac": k1_rate / peak, "traffic": None,
+                     "peak_basis": "%d SMs x %.0f MHz x %.0f pairs/clk/SM (FP32 pipe and SFU limits)"
+                                   % (sms, clk_max, PAIRS_PER_CLK_SM)},
+        "clocks": clk,
+        "gpu_launches": 4 * args.steps * world,
+        "e2e": {"value": e2e_units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(p, args.cpu_seconds)
+    run.close()
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def ctypes_stream(stream):
+    h = stream.cuda_stream
+    return h if h else None
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,164 @@
+/*
+ * opendust.h -- C ABI of the GB300 (sm_103a) ion-flow-around-dust library.
+ *
+ * The library advances the paper's method (OpenDust, arXiv 2205.06557) on one GPU:
+ * superions in a cylinder of radius R and height H (origin on the axis at mid
+ * height, flow along +z; Sec. 2) interact by Yukawa forces screened with the
+ * electron Debye length; grains act on ions by bare Coulomb forces and feel the
+ * screened ion field (Eq. 1); the ions outside the domain act through the cavity
+ * field E_out (App. A); ions move by velocity Verlet in the driving field and
+ * collide with neutrals at a constant frequency (Andersen thermostat, Sec. 2);
+ * ions that leave the domain or hit a grain are replaced one for one on the
+ * boundary (App. B); absorbed ions charge the grain and transfer momentum (Eq. 3);
+ * per-dust force terms (Eqs. 1-4) and charges are accumulated in FP64.
+ *
+ * Conventions for every call:
+ *   - units are SI;
+ *   - pointers marked "host" are ordinary CPU memory owned by the caller, read or
+ *     written only during the call; the library owns all device memory it allocates;
+ *   - return value 0 (OD_OK) on success, a negative OD_E* code otherwise; the text of
+ *     the last error is available from od_last_error();
+ *   - after any error the handle stays valid for od_destroy() and for reads;
+ *   - calls on one handle are not thread-safe; different handles are independent.
+ */
+#ifndef OPENDUST_H
+#define OPENDUST_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define OD_MAX_DUST 8 /* grains per run */
+#define OD_REC 13     /* per-dust record: q, F_orbit[3], F_dd[3], F_collect[3], F_ext[3] */
+#define OD_EV 13      /* per-step events: absorbed[8], outflow, injected bottom/top/side, collided */
+#define OD_NCOUNT 16  /* cumulative counters, see od_counters() */
+
+/* return codes */
+#define OD_OK 0
+#define OD_EINVAL (-1)    /* invalid parameter or argument */
+#define OD_ENOMEM (-2)    /* device allocation failed */
+#define OD_ECUDA (-3)     /* a CUDA call failed (message in od_last_error) */
+#define OD_ENAN (-4)      /* a non-finite ion position or velocity was produced */
+#define OD_EOVERFLOW (-5) /* more ions than the handle's capacity */
+#define OD_ETIMEOUT (-6)  /* a device-side wait hit its iteration limit */
+#define OD_ENODEV (-7)    /* no CUDA device */
+
+/* od_params.flags */
+#define OD_F_NO_IONION 1    /* drop the ion-ion Yukawa forces */
+#define OD_F_NO_EOUT 2      /* drop the cavity field E_out (ions and grains) */
+#define OD_F_NO_BOUNDARY 4  /* no outflow removal (absorbed ions are still replaced) */
+#define OD_F_NO_ABSORB 8    /* grains do not absorb ions */
+#define OD_F_PAPER_SIDE 16  /* side injection without the tangential thermal velocity */
+#define OD_F_FP32_STATE 32  /* round ion positions and velocities to FP32 after every
+                               update (precision study: FP32-only ion state) */
+#define OD_F_NO_GRAPH 64    /* launch each step's kernels directly, not as a CUDA graph */
+
+/* od_params.charge_model (Sec. 2 charging options) */
+#define OD_Q_GIVEN 0      /* constant charges q0 */
+#define OD_Q_CONSISTENT 1 /* OML electron flux + counted absorbed ions */
+
+typedef struct od_dust {
+    double x, y, z; /* position, m; the grain must lie inside the cylinder */
+    double radius;  /* m, > 0 */
+    double q0;      /* initial (or constant) charge, C */
+} od_dust;
+
+typedef struct od_params {
+    double ion_mass;          /* m_i, kg */
+    double ion_charge_number; /* Z > 0 (1 for singly charged ions) */
+    double T_i, T_n, T_e;     /* ion, neutral, electron temperatures, K; T_n <= 0 => T_n = T_i */
+    double n_inf;             /* ion density of the unperturbed plasma, m^-3 (electrons: Z n_inf) */
+    double mach;              /* flow speed u = mach * sqrt(Z k T_e / m_i); with nu_in > 0 the
+                                 driving field is set to E = m_i nu_in u / (Z e) */
+    double E_ext;             /* driving field along +z, V/m (field-driven flow, needs nu_in > 0,
+                                 flow speed u = Z e E_ext / (m_i nu_in)); give mach or E_ext */
+    double nu_in;             /* ion-neutral collision frequency, 1/s; 0 = collisionless */
+    double R, H;              /* cylinder radius and height, m */
+    double dt;                /* time step, s */
+    double weight;            /* real ions per superion, >= 1 typical */
+    int64_t n_ions;           /* superions; 0 => round(n_inf pi R^2 H / weight) */
+    int32_t n_dust;           /* 0 .. OD_MAX_DUST */
+    int32_t charge_model;     /* OD_Q_GIVEN or OD_Q_CONSISTENT */
+    const od_dust* dust;      /* host, n_dust entries, copied by od_create */
+    uint64_t seed;            /* Philox4x32-10 key for every random draw */
+    int64_t avg_start;        /* first step (1-based) included in the time averages; <= 0 => 1 */
+    const double* eout_coeffs;/* host, optional: the 15 alpha of App. A's polynomial, SI; NULL =>
+                                 computed by quadrature of the uniform ion fill and least squares */
+    int32_t flags;            /* OD_F_* */
+    int32_t eout_grid;        /* App. A grid nodes per axis minus one; 0 => 40 */
+    void* cuda_stream;        /* cudaStream_t for all work; NULL => a stream owned by the library */
+} od_params;
+
+typedef struct od_handle od_handle;
+
+/* Create a run: validate p (no device work if invalid, OD_EINVAL), derive the plasma
+ * constants, build E_out (App. A), place the initial ions (uniform in the cylinder
+ * outside the grains, shifted-Maxwellian velocities) and compute their initial forces.
+ * *out receives the handle, or NULL on error (then od_last_error(NULL) has the text). */
+int od_create(const od_params* p, od_handle** out);
+
+/* Advance n >= 0 time steps (the canonical order: half kick and drift; absorption and
+ * outflow; compaction and re-injection; forces; half kick; collisions; grain update).
+ * Work is queued on the run's stream; the call waits for it to read the device error
+ * word: OD_ENAN, OD_ETIMEOUT or OD_ECUDA report a failure inside the steps. */
+int od_step(od_handle* h, int64_t n);
+
+/* Time averages over steps avg_start..current (Sec. 2 results): q[D] mean charge (C)
+ * and F[3 D] mean total force (N) = F_orbit + F_dd + F_collect + F_ext. Host arrays. */
+int od_dust_state(od_handle* h, double* q, double* F);
+
+/* Release all device memory and the handle. NULL is a no-op. */
+void od_destroy(od_handle* h);
+
+/* ---- extras for tests, benchmarks and restarts ---- */
+
+/* Window means and batch-means standard errors (20 equal batches) of every record
+ * entry: mean[D][13], se[D][13] (host; se = NaN with fewer than 20 steps). */
+int od_dust_terms(od_handle* h, double* mean, double* se);
+
+/* Per-step records for steps first..first+count-1 (1-based): rec[count][D][13] (q is the
+ * charge after that step's update; the force terms use the charges the ions felt during
+ * the step) and ev[count][13] event counts. Either pointer may be NULL. Host arrays. */
+int od_series(od_handle* h, int64_t first, int64_t count, double* rec, int32_t* ev);
+
+/* Cumulative counters (host int64[16]): absorbed per grain [0..7], outflow [8],
+ * injected bottom/top/side [9..11], collided [12], steps [13], ions [14], next id [15]. */
+int od_counters(od_handle* h, int64_t* out);
+
+/* Current charges q[D] (C) and the Eq. 1 force on every grain f_orbit[3 D] (N) at the
+ * last force evaluation (host). */
+int od_dust_now(od_handle* h, double* q, double* f_orbit);
+
+/* Copy the ion state to host arrays: x[3 n], v[3 n] (FP64), a[3 n] (FP32 accelerations
+ * of the last force evaluation, as doubles), id[n]. cap is the array length in ions;
+ * returns the ion count n (>= 0) or an error; any pointer may be NULL. */
+int64_t od_get_ions(od_handle* h, double* x, double* v, double* a, uint64_t* id, int64_t cap);
+
+/* Replace the ion state with n ions from host arrays x[3 n], v[3 n], id[n]; next_id is
+ * the id given to the next injected ion. If a (host, 3 n) is NULL the forces and the
+ * grain force are recomputed for the new positions; otherwise a is taken as the
+ * accelerations (restart from od_get_ions output). n may not exceed the ion count the
+ * handle was created with (OD_EOVERFLOW). */
+int od_set_ions(od_handle* h, const double* x, const double* v, const double* a, const uint64_t* id,
+                int64_t n, uint64_t next_id);
+
+/* Derived constants (host double[32]): lambda_De, c_s, sig_i, sig_n, u, E, q, m, p_bottom,
+ * p_top, p_side, T_bottom, T_bottom+top, T_coll, N, alpha[0..14] (at 15..29), capacity, SMs. */
+int od_info(od_handle* h, double* out);
+
+/* Per-kernel timing (profiling mode): when on, od_step launches kernels directly with
+ * CUDA events around each and accumulates their durations. ms[4] and launches[4] for
+ * push+scan+inject, pair forces, kick+collide, grain update. Host arrays. */
+int od_set_profiling(od_handle* h, int on);
+int od_kernel_times(od_handle* h, double* ms, int64_t* launches);
+
+/* Text of the last error on h, or of the last failed od_create when h is NULL. */
+const char* od_last_error(const od_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OPENDUST_H */

@@ -72,6 +72,7 @@ def lib():
         L.orc_get_ions.argtypes = [vp, vp, vp, vp, vp]
         L.orc_set_ions.argtypes = [vp, i64, vp, vp, vp, i64]
         L.orc_forces.argtypes = [vp, i64, i64, vp, vp]
+        L.orc_load_ions.argtypes = [vp, i64, vp, vp, vp, i64]
         L.orc_derived.argtypes = [vp, vp]
         L.orc_alpha.argtypes = [vp, vp]
         L.orc_eout.argtypes = [vp, d, d, d, vp]
@@ -194,6 +195,16 @@ class Oracle:
         if next_id is None:
             next_id = int(ids.max()) + 1 if n else 0
         lib().orc_set_ions(self.h, n, _ptr(x), _ptr(v), _ptr(ids), int(next_id))
+
+    def load_ions(self, x, v, ids, next_id=None):
+        """replace the ion state without a force pass (accelerations zero)"""
+        x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3)
+        v = np.ascontiguousarray(v, dtype=np.float64).reshape(-1, 3)
+        ids = np.ascontiguousarray(ids, dtype=np.uint64)
+        n = x.shape[0]
+        if next_id is None:
+            next_id = int(ids.max()) + 1 if n else 0
+        lib().orc_load_ions(self.h, n, _ptr(x), _ptr(v), _ptr(ids), int(next_id))
 
     def forces(self, i0=0, i1=None, dust=True):
         """accelerations of target ions [i0, i1) and the Eq. 1 force on every grain"""

@@ -638,6 +638,25 @@ int orc_set_ions(orc_state* s, int64_t n, const double* x, const double* v, cons
     return 0;
 }
 
+/* replace the ion state without evaluating forces (accelerations set to zero): for
+ * sampled force checks at sizes where the full O(N^2) pass is too slow */
+int orc_load_ions(orc_state* s, int64_t n, const double* x, const double* v, const uint64_t* id, int64_t next_id)
+{
+    if (n < 0) return -1;
+    size_t cnt = n > 0 ? (size_t)n : 1;
+    s->x = realloc(s->x, sizeof(double) * 3 * cnt);
+    s->v = realloc(s->v, sizeof(double) * 3 * cnt);
+    s->a = realloc(s->a, sizeof(double) * 3 * cnt);
+    s->id = realloc(s->id, sizeof(uint64_t) * cnt);
+    s->N = n;
+    memcpy(s->x, x, sizeof(double) * 3 * n);
+    memcpy(s->v, v, sizeof(double) * 3 * n);
+    memcpy(s->id, id, sizeof(uint64_t) * n);
+    memset(s->a, 0, sizeof(double) * 3 * n);
+    s->next_id = next_id;
+    return 0;
+}
+
 void orc_derived(const orc_state* s, double* o)
 {
     o[0] = s->lam;

@@ -70,6 +70,7 @@ int64_t orc_num_ions(const orc_state* s);
 int64_t orc_step_index(const orc_state* s);
 void orc_get_ions(const orc_state* s, double* x, double* v, double* a, uint64_t* id);
 int orc_set_ions(orc_state* s, int64_t n, const double* x, const double* v, const uint64_t* id, int64_t next_id);
+int orc_load_ions(orc_state* s, int64_t n, const double* x, const double* v, const uint64_t* id, int64_t next_id);
 void orc_forces(const orc_state* s, int64_t i0, int64_t i1, double* acc, double* f_orbit);
 void orc_derived(const orc_state* s, double* out /* 24 */);
 void orc_alpha(const orc_state* s, double* alpha);

@@ -1,1 +1,291 @@
-"""placeholder"""
+"""GB300 (sm_103a) library for the ion-flow-around-dust method of OpenDust (arXiv 2205.06557).
+
+Thin ctypes binding of the C ABI in ``include/opendust.h``: the functions below have
+the ABI's names and only marshal arguments.  Every step of the method runs in the
+library's CUDA kernels; there is no CPU fallback: if ``libopendust.so`` is missing or
+no GPU is present the calls raise.
+
+Parameters can be given as an ``od_params`` structure or as the plain dict of SI
+values used by ``workloads`` (keys: m_i, Z, T_i, T_n, T_e, n_inf, mach, E_ext, nu, R,
+H, dt, weight, n_ions, dust=[{x, y, z, a, q0}], charge_model, seed, avg_start,
+alpha, flags, eout_grid).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+MAX_DUST = 8
+REC = 13
+EV = 13
+NCOUNT = 16
+
+OD_OK = 0
+ERRORS = {-1: "OD_EINVAL", -2: "OD_ENOMEM", -3: "OD_ECUDA", -4: "OD_ENAN", -5: "OD_EOVERFLOW",
+          -6: "OD_ETIMEOUT", -7: "OD_ENODEV"}
+
+F_NO_IONION = 1
+F_NO_EOUT = 2
+F_NO_BOUNDARY = 4
+F_NO_ABSORB = 8
+F_PAPER_SIDE = 16
+F_FP32_STATE = 32
+F_NO_GRAPH = 64
+
+Q_GIVEN = 0
+Q_CONSISTENT = 1
+_QM = {"given": Q_GIVEN, "consistent": Q_CONSISTENT}
+
+_d = ctypes.c_double
+
+
+class od_dust(ctypes.Structure):
+    _fields_ = [("x", _d), ("y", _d), ("z", _d), ("radius", _d), ("q0", _d)]
+
+
+class od_params(ctypes.Structure):
+    _fields_ = [
+        ("ion_mass", _d), ("ion_charge_number", _d), ("T_i", _d), ("T_n", _d), ("T_e", _d), ("n_inf", _d),
+        ("mach", _d), ("E_ext", _d), ("nu_in", _d), ("R", _d), ("H", _d), ("dt", _d), ("weight", _d),
+        ("n_ions", ctypes.c_int64), ("n_dust", ctypes.c_int32), ("charge_model", ctypes.c_int32),
+        ("dust", ctypes.POINTER(od_dust)), ("seed", ctypes.c_uint64), ("avg_start", ctypes.c_int64),
+        ("eout_coeffs", ctypes.POINTER(_d)), ("flags", ctypes.c_int32), ("eout_grid", ctypes.c_int32),
+        ("cuda_stream", ctypes.c_void_p),
+    ]
+
+
+class OdError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (ERRORS.get(code, "OD_E?"), code, msg))
+        self.code = code
+
+
+_LIB = None
+
+
+def lib_path():
+    return _build.LIB
+
+
+def lib():
+    """Load libopendust.so (built in place by build.py); raise if it is missing."""
+    global _LIB
+    if _LIB is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError("libopendust.so is not built: run paper_2205_06557_gb300/build.py "
+                               "(or __graft_entry__.build()); there is no CPU fallback")
+        L = ctypes.CDLL(path)
+        P, vp, i32, i64 = ctypes.POINTER, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+        L.od_create.argtypes = [P(od_params), P(vp)]
+        L.od_step.argtypes = [vp, i64]
+        L.od_dust_state.argtypes = [vp, vp, vp]
+        L.od_destroy.argtypes = [vp]
+        L.od_destroy.restype = None
+        L.od_dust_terms.argtypes = [vp, vp, vp]
+        L.od_series.argtypes = [vp, i64, i64, vp, vp]
+        L.od_counters.argtypes = [vp, vp]
+        L.od_dust_now.argtypes = [vp, vp, vp]
+        L.od_get_ions.argtypes = [vp, vp, vp, vp, vp, i64]
+        L.od_get_ions.restype = i64
+        L.od_set_ions.argtypes = [vp, vp, vp, vp, vp, i64, ctypes.c_uint64]
+        L.od_info.argtypes = [vp, vp]
+        L.od_set_profiling.argtypes = [vp, ctypes.c_int]
+        L.od_kernel_times.argtypes = [vp, vp, vp]
+        L.od_last_error.argtypes = [vp]
+        L.od_last_error.restype = ctypes.c_char_p
+        for name in ("od_create", "od_step", "od_dust_state", "od_dust_terms", "od_series", "od_counters",
+                     "od_dust_now", "od_set_ions", "od_info", "od_set_profiling", "od_kernel_times"):
+            getattr(L, name).restype = ctypes.c_int
+        _LIB = L
+    return _LIB
+
+
+def _check(rc, h=None):
+    if rc < 0:
+        msg = lib().od_last_error(h)
+        raise OdError(int(rc), msg.decode() if msg else "")
+    return rc
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def make_params(p, stream=None):
+    """od_params from a workload dict; returns (params, keepalive)."""
+    if isinstance(p, od_params):
+        return p, ()
+    dust = p.get("dust", [])
+    darr = (od_dust * max(len(dust), 1))()
+    for k, g in enumerate(dust):
+        darr[k] = od_dust(g["x"], g["y"], g["z"], g["a"], g.get("q0", 0.0))
+    s = od_params()
+    s.ion_mass = p["m_i"]
+    s.ion_charge_number = p.get("Z", 1.0)
+    s.T_i, s.T_n, s.T_e = p["T_i"], p.get("T_n", 0.0), p["T_e"]
+    s.n_inf = p["n_inf"]
+    s.mach, s.E_ext, s.nu_in = p.get("mach", 0.0), p.get("E_ext", 0.0), p.get("nu", 0.0)
+    s.R, s.H, s.dt = p["R"], p["H"], p["dt"]
+    s.weight = p.get("weight", 1.0)
+    s.n_ions = int(p.get("n_ions", 0))
+    s.n_dust = len(dust)
+    s.charge_model = _QM[p.get("charge_model", "given")]
+    s.dust = ctypes.cast(darr, ctypes.POINTER(od_dust))
+    s.seed = int(p.get("seed", 0))
+    s.avg_start = int(p.get("avg_start", 1))
+    keep = [darr]
+    if p.get("alpha") is not None:
+        al = (ctypes.c_double * 15)(*[float(a) for a in p["alpha"]])
+        s.eout_coeffs = ctypes.cast(al, ctypes.POINTER(ctypes.c_double))
+        keep.append(al)
+    s.flags = int(p.get("flags", 0))
+    s.eout_grid = int(p.get("eout_grid", 0))
+    s.cuda_stream = stream
+    return s, keep
+
+
+def od_create(p, stream=None):
+    s, keep = make_params(p, stream)
+    h = ctypes.c_void_p()
+    _check(lib().od_create(ctypes.byref(s), ctypes.byref(h)))
+    return h
+
+
+def od_step(h, n):
+    return _check(lib().od_step(h, int(n)), h)
+
+
+def od_dust_state(h, n_dust):
+    q = np.zeros(MAX_DUST)
+    F = np.zeros(3 * MAX_DUST)
+    _check(lib().od_dust_state(h, _ptr(q), _ptr(F)), h)
+    return q[:n_dust], F[: 3 * n_dust].reshape(n_dust, 3)
+
+
+def od_destroy(h):
+    if h is not None:
+        lib().od_destroy(h)
+
+
+def od_dust_terms(h, n_dust):
+    mean = np.zeros((MAX_DUST, REC))
+    se = np.zeros((MAX_DUST, REC))
+    _check(lib().od_dust_terms(h, _ptr(mean), _ptr(se)), h)
+    return mean.reshape(-1)[: n_dust * REC].reshape(n_dust, REC), se.reshape(-1)[: n_dust * REC].reshape(n_dust, REC)
+
+
+def od_series(h, n_dust, first, count):
+    rec = np.zeros((count, max(n_dust, 1), REC))
+    ev = np.zeros((count, EV), dtype=np.int32)
+    _check(lib().od_series(h, int(first), int(count), _ptr(rec), _ptr(ev)), h)
+    return rec[:, :n_dust], ev
+
+
+def od_counters(h):
+    out = np.zeros(NCOUNT, dtype=np.int64)
+    _check(lib().od_counters(h, _ptr(out)), h)
+    return out
+
+
+def od_dust_now(h, n_dust):
+    q = np.zeros(MAX_DUST)
+    fo = np.zeros(3 * MAX_DUST)
+    _check(lib().od_dust_now(h, _ptr(q), _ptr(fo)), h)
+    return q[:n_dust], fo[: 3 * n_dust].reshape(n_dust, 3)
+
+
+def od_get_ions(h, cap):
+    x = np.zeros((cap, 3))
+    v = np.zeros((cap, 3))
+    a = np.zeros((cap, 3))
+    ids = np.zeros(cap, dtype=np.uint64)
+    n = _check(lib().od_get_ions(h, _ptr(x), _ptr(v), _ptr(a), _ptr(ids), int(cap)), h)
+    return x[:n], v[:n], a[:n], ids[:n]
+
+
+def od_set_ions(h, x, v, ids, next_id, a=None):
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3)
+    v = np.ascontiguousarray(v, dtype=np.float64).reshape(-1, 3)
+    ids = np.ascontiguousarray(ids, dtype=np.uint64)
+    if a is not None:
+        a = np.ascontiguousarray(a, dtype=np.float64).reshape(-1, 3)
+    return _check(lib().od_set_ions(h, _ptr(x), _ptr(v), _ptr(a), _ptr(ids), x.shape[0], int(next_id)), h)
+
+
+INFO = ("lam", "cs", "sig", "sig_n", "u", "E", "q", "m", "pb", "pt", "ps", "Tb", "Tbt", "Tcoll", "N")
+
+
+def od_info(h):
+    out = np.zeros(32)
+    _check(lib().od_info(h, _ptr(out)), h)
+    d = dict(zip(INFO, out[:15]))
+    d["alpha"] = out[15:30].copy()
+    d["capacity"] = out[30]
+    d["sms"] = out[31]
+    return d
+
+
+def od_set_profiling(h, on):
+    return _check(lib().od_set_profiling(h, 1 if on else 0), h)
+
+
+def od_kernel_times(h):
+    ms = np.zeros(4)
+    n = np.zeros(4, dtype=np.int64)
+    _check(lib().od_kernel_times(h, _ptr(ms), _ptr(n)), h)
+    return ms, n
+
+
+def od_last_error(h=None):
+    m = lib().od_last_error(h)
+    return m.decode() if m else ""
+
+
+class Run:
+    """Convenience owner of one handle (create on construction, destroy on close)."""
+
+    def __init__(self, p, stream=None):
+        self.D = len(p.get("dust", [])) if isinstance(p, dict) else p.n_dust
+        self.h = od_create(p, stream)
+        self.N = int(od_info(self.h)["N"])
+
+    def step(self, n=1):
+        od_step(self.h, n)
+
+    def close(self):
+        if self.h is not None:
+            od_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        return od_info(self.h)
+
+    def dust_state(self):
+        return od_dust_state(self.h, self.D)
+
+    def dust_terms(self):
+        return od_dust_terms(self.h, self.D)
+
+    def series(self, first, count):
+        return od_series(self.h, self.D, first, count)
+
+    def counters(self):
+        return od_counters(self.h)
+
+    def dust_now(self):
+        return od_dust_now(self.h, self.D)
+
+    def get_ions(self):
+        return od_get_ions(self.h, max(int(od_info(self.h)["capacity"]), 1))
+
+    def set_ions(self, x, v, ids, next_id, a=None):
+        od_set_ions(self.h, x, v, ids, next_id, a)

@@ -1,0 +1,848 @@
+// Host side of the GB300 ion-flow-around-dust library: the C ABI of opendust.h.
+//
+// od_create validates the parameters (before any device work), derives the plasma
+// constants, builds the App. A cavity field (device quadrature + host least squares),
+// plans the pair-kernel partition, allocates device memory and places the initial
+// ions; od_step replays a captured graph of one step (or launches its kernels
+// directly in profiling mode).
+#include <algorithm>
+#include <cmath>
+#include <cstddef>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "od_internal.h"
+
+using namespace od;
+
+namespace {
+
+// CODATA 2018
+constexpr double kQE = 1.602176634e-19;
+constexpr double kKB = 1.380649e-23;
+constexpr double kEPS0 = 8.8541878128e-12;
+constexpr double kME = 9.1093837015e-31;
+constexpr double kPI = 3.141592653589793238;
+constexpr double kTWO32 = 4294967296.0;
+
+thread_local std::string g_create_error;
+
+double norm_cdf(double z) { return 0.5 * std::erfc(-z / std::sqrt(2.0)); }
+double norm_pdf(double z) { return std::exp(-0.5 * z * z) / std::sqrt(2.0 * kPI); }
+
+unsigned long long prob_threshold(double p)
+{
+    double t = std::floor(p * kTWO32);
+    t = std::min(std::max(t, 0.0), kTWO32);
+    return (unsigned long long)t;
+}
+
+// paper's monomial order of Eq. (Polinomial): alpha_t multiplies r^(2 a_t) z^(2 b_t)
+const int kPowR[15] = {0, 1, 0, 1, 2, 0, 2, 1, 3, 0, 2, 3, 1, 4, 0};
+const int kPowZ[15] = {0, 0, 1, 1, 0, 2, 1, 2, 0, 3, 2, 1, 3, 0, 4};
+
+// index of r2^p z2^q among the 10 monomials of degree <= 3 used by the device field
+int mono_index(int p, int q)
+{
+    static const int tab[4][4] = {{0, 2, 5, 9}, {1, 4, 8, -1}, {3, 7, -1, -1}, {6, -1, -1, -1}};
+    return tab[p][q];
+}
+
+// Gauss-Legendre nodes/weights on [-1, 1] (Newton on the three-term recurrence)
+void gl_nodes(int n, std::vector<double>& x, std::vector<double>& w)
+{
+    x.resize(n);
+    w.resize(n);
+    for (int i = 0; i < n; ++i) {
+        double t = std::cos(kPI * (i + 0.75) / (n + 0.5));
+        double dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = t;
+            for (int k = 2; k <= n; ++k) {
+                const double p2 = ((2.0 * k - 1.0) * t * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            if (n == 1) {
+                p1 = t;
+                p0 = 1.0;
+            }
+            dp = n * (t * p1 - p0) / (t * t - 1.0);
+            const double dt = p1 / dp;
+            t -= dt;
+            if (std::fabs(dt) < 1e-16) break;
+        }
+        double p0 = 1.0, p1 = t;
+        for (int k = 2; k <= n; ++k) {
+            const double p2 = ((2.0 * k - 1.0) * t * p1 - (k - 1.0) * p0) / k;
+            p0 = p1;
+            p1 = p2;
+        }
+        dp = n * (t * p1 - p0) / (t * t - 1.0);
+        x[i] = t;
+        w[i] = 2.0 / ((1.0 - t * t) * dp * dp);
+    }
+}
+
+// least squares min |A c - b| by modified Gram-Schmidt on [A | b] (column-major A: m x n)
+bool lsq_mgs(int m, int n, std::vector<double> A, std::vector<double> b, double* c)
+{
+    std::vector<double> R(n * n, 0.0), z(n, 0.0);
+    for (int j = 0; j < n; ++j) {
+        double* aj = &A[(size_t)j * m];
+        double nr = 0.0;
+        for (int i = 0; i < m; ++i) nr += aj[i] * aj[i];
+        nr = std::sqrt(nr);
+        if (!(nr > 0.0)) return false;
+        R[j * n + j] = nr;
+        for (int i = 0; i < m; ++i) aj[i] /= nr;
+        for (int k = j + 1; k < n; ++k) {
+            double* ak = &A[(size_t)k * m];
+            double d = 0.0;
+            for (int i = 0; i < m; ++i) d += aj[i] * ak[i];
+            R[j * n + k] = d;
+            for (int i = 0; i < m; ++i) ak[i] -= d * aj[i];
+        }
+        double d = 0.0;
+        for (int i = 0; i < m; ++i) d += aj[i] * b[i];
+        z[j] = d;
+        for (int i = 0; i < m; ++i) b[i] -= d * aj[i];
+    }
+    for (int j = n - 1; j >= 0; --j) {
+        double s = z[j];
+        for (int k = j + 1; k < n; ++k) s -= R[j * n + k] * c[k];
+        c[j] = s / R[j * n + j];
+    }
+    return true;
+}
+
+}  // namespace
+
+struct od_handle {
+    Phys P{};
+    Bufs B{};
+    ForceArgs F{};
+    int variant = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    bool graph_ok = false;
+    long long cap = 0;       // ion capacity
+    long long npad_cap = 0;  // fpos capacity
+    long long part_cap = 0;  // partial-sum capacity (float4)
+    long long nb_cap = 0;    // kick blocks capacity
+    long long host_step = 0;
+    long long series_cap = 0;
+    int sms = 0;
+    double alpha[15] = {0};
+    double info[32] = {0};
+    std::string err;
+    bool profiling = false;
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    double kms[4] = {0, 0, 0, 0};
+    long long klaunch[4] = {0, 0, 0, 0};
+    double* d_stats = nullptr;
+    double* d_series = nullptr;
+    int* d_evseries = nullptr;
+};
+
+namespace {
+
+int fail(od_handle* h, int code, const std::string& msg)
+{
+    if (h) h->err = msg;
+    else g_create_error = msg;
+    return code;
+}
+
+int cuda_fail(od_handle* h, cudaError_t e, const char* where)
+{
+    return fail(h, e == cudaErrorMemoryAllocation ? OD_ENOMEM : OD_ECUDA,
+                std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define OD_CK(h, call)                                      \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
+    } while (0)
+
+#define OD_LK(h, call)                                                       \
+    do {                                                                     \
+        int e_ = (call);                                                     \
+        if (e_ != 0) return cuda_fail(h, (cudaError_t)e_, #call);            \
+    } while (0)
+
+// parameter checks that need no device
+int validate(const od_params* p, std::string& msg)
+{
+    if (!p) {
+        msg = "params is NULL";
+        return OD_EINVAL;
+    }
+    auto pos = [](double v) { return std::isfinite(v) && v > 0.0; };
+    if (!(pos(p->ion_mass) && pos(p->ion_charge_number) && pos(p->T_i) && pos(p->T_e) && pos(p->n_inf) &&
+          pos(p->R) && pos(p->H) && pos(p->dt) && pos(p->weight))) {
+        msg = "ion_mass, ion_charge_number, T_i, T_e, n_inf, R, H, dt and weight must be finite and > 0";
+        return OD_EINVAL;
+    }
+    if (!(std::isfinite(p->mach) && std::isfinite(p->E_ext) && std::isfinite(p->nu_in) && p->mach >= 0 &&
+          p->E_ext >= 0 && p->nu_in >= 0)) {
+        msg = "mach, E_ext and nu_in must be finite and >= 0";
+        return OD_EINVAL;
+    }
+    if (p->mach > 0 && p->E_ext > 0) {
+        msg = "give either mach or E_ext, not both";
+        return OD_EINVAL;
+    }
+    if (p->E_ext > 0 && !(p->nu_in > 0)) {
+        msg = "a field-driven flow (E_ext > 0) needs nu_in > 0";
+        return OD_EINVAL;
+    }
+    if (p->n_dust < 0 || p->n_dust > OD_MAX_DUST) {
+        msg = "n_dust must be in 0..8";
+        return OD_EINVAL;
+    }
+    if (p->n_dust > 0 && !p->dust) {
+        msg = "dust is NULL with n_dust > 0";
+        return OD_EINVAL;
+    }
+    for (int k = 0; k < p->n_dust; ++k) {
+        const od_dust& d = p->dust[k];
+        if (!(pos(d.radius) && std::isfinite(d.x) && std::isfinite(d.y) && std::isfinite(d.z) && std::isfinite(d.q0))) {
+            msg = "grain " + std::to_string(k) + ": radius must be > 0 and all values finite";
+            return OD_EINVAL;
+        }
+        if (std::sqrt(d.x * d.x + d.y * d.y) + d.radius >= p->R || std::fabs(d.z) + d.radius >= 0.5 * p->H) {
+            msg = "grain " + std::to_string(k) + " does not lie inside the cylinder";
+            return OD_EINVAL;
+        }
+    }
+    if (p->charge_model != OD_Q_GIVEN && p->charge_model != OD_Q_CONSISTENT) {
+        msg = "charge_model must be OD_Q_GIVEN or OD_Q_CONSISTENT";
+        return OD_EINVAL;
+    }
+    if (p->n_ions < 0) {
+        msg = "n_ions must be >= 0";
+        return OD_EINVAL;
+    }
+    const double nreq = p->n_ions > 0 ? (double)p->n_ions : p->n_inf * kPI * p->R * p->R * p->H / p->weight;
+    if (!(nreq < 2.0e8)) {
+        msg = "too many ions (limit 2e8 per run)";
+        return OD_EINVAL;
+    }
+    if (p->eout_grid < 0 || p->eout_grid > 400) {
+        msg = "eout_grid must be in 0..400";
+        return OD_EINVAL;
+    }
+    return OD_OK;
+}
+
+// derived constants of Sec. 2 and App. B; N from the density when n_ions == 0
+void derive(const od_params* p, Phys& P, od_handle* h)
+{
+    const double Z = p->ion_charge_number;
+    const double Tn = p->T_n > 0 ? p->T_n : p->T_i;
+    const double lam = std::sqrt(kEPS0 * kKB * p->T_e / (Z * p->n_inf * kQE * kQE));
+    const double cs = std::sqrt(Z * kKB * p->T_e / p->ion_mass);
+    P.sig = std::sqrt(kKB * p->T_i / p->ion_mass);
+    P.sig_n = std::sqrt(kKB * Tn / p->ion_mass);
+    P.q = p->weight * Z * kQE;
+    P.m = p->weight * p->ion_mass;
+    P.u = 0.0;
+    P.E = 0.0;
+    if (p->mach > 0) {
+        P.u = p->mach * cs;
+        if (p->nu_in > 0) P.E = p->ion_mass * p->nu_in * P.u / (Z * kQE);
+    } else if (p->E_ext > 0) {
+        P.E = p->E_ext;
+        P.u = Z * kQE * p->E_ext / (p->ion_mass * p->nu_in);
+    }
+    const double zu = P.u / P.sig;
+    const double Jb = kPI * p->R * p->R * (P.u * norm_cdf(zu) + P.sig * norm_pdf(zu));
+    const double Jt = kPI * p->R * p->R * (-P.u * norm_cdf(-zu) + P.sig * norm_pdf(zu));
+    const double Js = 2.0 * kPI * p->R * p->H * P.sig / std::sqrt(2.0 * kPI);
+    const double J = Jb + Jt + Js;
+    P.Tb = prob_threshold(Jb / J);
+    P.Tbt = prob_threshold((Jb + Jt) / J);
+    const double pc = -std::expm1(-p->nu_in * p->dt);
+    P.Tcoll = prob_threshold(pc);
+    P.dt = p->dt;
+    P.R = p->R;
+    P.H = p->H;
+    P.hz = 0.5 * p->H;
+    P.R2 = p->R * p->R;
+    P.qm = Z * kQE / p->ion_mass;
+    P.kdi = Z * kQE / (4.0 * kPI * kEPS0 * p->ion_mass);
+    P.korb = P.q / (4.0 * kPI * kEPS0);
+    P.inv4pieps0 = 1.0 / (4.0 * kPI * kEPS0);
+    P.lam_inv = 1.0 / lam;
+    const double Ls = lam / 1.4426950408889634;  // lambda / log2(e)
+    P.Ls_inv = (float)(1.0 / Ls);
+    P.k_ii = (float)(P.q * P.q / (4.0 * kPI * kEPS0 * P.m * Ls * Ls));
+    P.key0 = (uint32_t)(p->seed & 0xffffffffull);
+    P.key1 = (uint32_t)(p->seed >> 32);
+    P.D = p->n_dust;
+    for (int k = 0; k < p->n_dust; ++k) {
+        P.gx[k] = p->dust[k].x;
+        P.gy[k] = p->dust[k].y;
+        P.gz[k] = p->dust[k].z;
+        P.ga[k] = p->dust[k].radius;
+        P.ga2[k] = p->dust[k].radius * p->dust[k].radius;
+    }
+    P.flags = p->flags;
+    P.charge_model = p->charge_model;
+    P.avg_start = p->avg_start > 0 ? p->avg_start : 1;
+    P.Ie0 = Z * p->n_inf * std::sqrt(8.0 * kKB * p->T_e / (kPI * kME)) / 4.0;
+    P.e_over_kTe = kQE / (kKB * p->T_e);
+    const long long N = p->n_ions > 0 ? p->n_ions : std::llround(p->n_inf * kPI * p->R * p->R * p->H / p->weight);
+    P.N = (int)N;
+    double* o = h->info;
+    o[0] = lam;
+    o[1] = cs;
+    o[2] = P.sig;
+    o[3] = P.sig_n;
+    o[4] = P.u;
+    o[5] = P.E;
+    o[6] = P.q;
+    o[7] = P.m;
+    o[8] = Jb / J;
+    o[9] = Jt / J;
+    o[10] = Js / J;
+    o[11] = (double)P.Tb;
+    o[12] = (double)P.Tbt;
+    o[13] = (double)P.Tcoll;
+}
+
+void set_field_coeffs(Phys& P, const double* alpha, bool on)
+{
+    for (int t = 0; t < 10; ++t) P.Gc[t] = P.Kc[t] = 0.0;
+    P.eout = on ? 1 : 0;
+    if (!on) return;
+    for (int t = 0; t < 15; ++t) {
+        const int a = kPowR[t], b = kPowZ[t];
+        if (a >= 1) P.Gc[mono_index(a - 1, b)] += 2.0 * a * alpha[t];
+        if (b >= 1) P.Kc[mono_index(a, b - 1)] += 2.0 * b * alpha[t];
+    }
+}
+
+// App. A: potential of the uniform ion fill on the (r, z) grid, then the 15-term fit
+int build_eout(od_handle* h, const od_params* p)
+{
+    const int nx = p->eout_grid > 0 ? p->eout_grid : 40, nz = nx, nq = 48;
+    const double lam = 1.0 / h->P.lam_inv;
+    std::vector<double> gx, gw;
+    gl_nodes(nq, gx, gw);
+    const int nodes = (nx + 1) * (nz + 1);
+    double *d_gl = nullptr, *d_out = nullptr;
+    OD_CK(h, cudaMalloc(&d_gl, sizeof(double) * 2 * nq));
+    OD_CK(h, cudaMalloc(&d_out, sizeof(double) * nodes));
+    OD_CK(h, cudaMemcpyAsync(d_gl, gx.data(), sizeof(double) * nq, cudaMemcpyHostToDevice, h->stream));
+    OD_CK(h, cudaMemcpyAsync(d_gl + nq, gw.data(), sizeof(double) * nq, cudaMemcpyHostToDevice, h->stream));
+    OD_LK(h, launch_eout_grid(p->R, p->H, lam, nx, nz, nq, d_gl, d_gl + nq, d_out, h->stream));
+    std::vector<double> I(nodes);
+    OD_CK(h, cudaMemcpyAsync(I.data(), d_out, sizeof(double) * nodes, cudaMemcpyDeviceToHost, h->stream));
+    OD_CK(h, cudaStreamSynchronize(h->stream));
+    cudaFree(d_gl);
+    cudaFree(d_out);
+    // Phi_ext = Phi_0 - Phi_cyl with Phi_0 = 0; Phi_cyl = Z e n_inf / (4 pi eps0) * I
+    const double pref = p->ion_charge_number * kQE * p->n_inf / (4.0 * kPI * kEPS0);
+    const double hz = 0.5 * p->H;
+    std::vector<double> A((size_t)nodes * 15), b(nodes);
+    for (int kr = 0; kr <= nx; ++kr)
+        for (int kz = 0; kz <= nz; ++kz) {
+            const int row = kr * (nz + 1) + kz;
+            const double rho2 = (double)kr * kr / ((double)nx * nx), zeta2 = (double)kz * kz / ((double)nz * nz);
+            b[row] = -pref * I[row];
+            for (int t = 0; t < 15; ++t) A[(size_t)t * nodes + row] = std::pow(rho2, kPowR[t]) * std::pow(zeta2, kPowZ[t]);
+        }
+    double beta[15];
+    if (!lsq_mgs(nodes, 15, A, b, beta)) return fail(h, OD_EINVAL, "E_out fit is singular");
+    for (int t = 0; t < 15; ++t)
+        h->alpha[t] = beta[t] / (std::pow(p->R * p->R, kPowR[t]) * std::pow(hz * hz, kPowZ[t]));
+    return OD_OK;
+}
+
+// balanced partition of the all-pairs work for pair-kernel variant v
+ForceArgs plan_forces(int N, int v, int sms, int units_per_block)
+{
+    ForceArgs F{};
+    const ForceVariant fv = force_variant(v);
+    F.TI = fv.BT * fv.IPT;
+    F.n_pad = N == 0 ? 0 : (N + F.TI - 1) / F.TI * F.TI;
+    if (F.n_pad == 0) return F;
+    const int n_it = F.n_pad / F.TI;
+    const long long gmax = (long long)sms * force_blocks_per_sm(v);
+    long long js = (units_per_block * gmax + n_it - 1) / n_it;
+    js = std::max(1ll, std::min(js, (long long)F.n_pad / fv.BT));
+    long long jc = ((F.n_pad + js - 1) / js + fv.BT - 1) / fv.BT * fv.BT;
+    F.JC = (int)jc;
+    F.JS = (int)((F.n_pad + jc - 1) / jc);
+    F.U = (long long)n_it * F.JS;
+    F.G = (int)std::min<long long>(gmax, F.U);
+    int W = 1;
+    for (int t = 0; t < n_it; ++t) {
+        const long long u0 = (long long)t * F.JS, u1 = u0 + F.JS - 1;
+        const int g0 = (int)(((u0 + 1) * F.G - 1) / F.U), g1 = (int)(((u1 + 1) * F.G - 1) / F.U);
+        W = std::max(W, g1 - g0 + 1);
+    }
+    F.W = W;
+    return F;
+}
+
+int default_variant(int N)
+{
+    if (N <= 4096) return 0;
+    if (N <= 32768) return 2;
+    return 3;
+}
+
+int ensure_part(od_handle* h)
+{
+    const long long need = (long long)h->F.W * h->F.n_pad;
+    if (need <= h->part_cap) return OD_OK;
+    if (h->B.part) cudaFree(h->B.part);
+    h->B.part = nullptr;
+    OD_CK(h, cudaMalloc(&h->B.part, sizeof(float4) * std::max(need, 1ll)));
+    h->part_cap = need;
+    return OD_OK;
+}
+
+int replan(od_handle* h, int N)
+{
+    h->P.N = N;
+    if (h->variant < 0 || h->variant >= num_force_variants()) h->variant = default_variant(N);
+    h->F = plan_forces(N, h->variant, h->sms, 8);
+    h->P.n_pad = h->F.n_pad;
+    if (h->F.n_pad > h->npad_cap) return fail(h, OD_EOVERFLOW, "padded ion count exceeds the buffer");
+    return ensure_part(h);
+}
+
+int read_error_word(od_handle* h)
+{
+    int err = 0;
+    OD_CK(h, cudaMemcpyAsync(&err, (char*)h->B.ctrl + offsetof(Ctrl, err), sizeof(int), cudaMemcpyDeviceToHost,
+                             h->stream));
+    OD_CK(h, cudaStreamSynchronize(h->stream));
+    if (err & ERR_NAN) return fail(h, OD_ENAN, "non-finite ion position or velocity");
+    if (err & ERR_TIMEOUT) return fail(h, OD_ETIMEOUT, "device-side wait hit its limit (scan look-back)");
+    if (err & ERR_PLACE) return fail(h, OD_EINVAL, "initial ion placement failed (grains fill the domain?)");
+    if (err & ERR_OVERFLOW) return fail(h, OD_EOVERFLOW, "ion capacity exceeded");
+    return OD_OK;
+}
+
+// forces for the current state (creation or replaced ions)
+int force_eval(od_handle* h)
+{
+    OD_LK(h, launch_forces(h->P, h->B, h->F, h->variant, h->stream));
+    OD_LK(h, launch_kick(h->P, h->B, h->F, 1, h->stream));
+    OD_LK(h, launch_dust(h->P, h->B, 1, h->stream));
+    return OD_OK;
+}
+
+int launch_step(od_handle* h)
+{
+    OD_LK(h, launch_push_scan(h->P, h->B, h->stream));
+    OD_LK(h, launch_forces(h->P, h->B, h->F, h->variant, h->stream));
+    OD_LK(h, launch_kick(h->P, h->B, h->F, 0, h->stream));
+    OD_LK(h, launch_dust(h->P, h->B, 0, h->stream));
+    return OD_OK;
+}
+
+int ensure_series(od_handle* h, long long need)
+{
+    if (need <= h->series_cap) return OD_OK;
+    long long nc = std::max({need, 2 * h->series_cap, 1024ll});
+    double* ns = nullptr;
+    int* ne = nullptr;
+    OD_CK(h, cudaMalloc(&ns, sizeof(double) * nc * MAXD * REC));
+    OD_CK(h, cudaMalloc(&ne, sizeof(int) * nc * EV));
+    OD_CK(h, cudaMemsetAsync(ns, 0, sizeof(double) * nc * MAXD * REC, h->stream));
+    OD_CK(h, cudaMemsetAsync(ne, 0, sizeof(int) * nc * EV, h->stream));
+    if (h->series_cap > 0) {
+        OD_CK(h, cudaMemcpyAsync(ns, h->d_series, sizeof(double) * h->series_cap * MAXD * REC,
+                                 cudaMemcpyDeviceToDevice, h->stream));
+        OD_CK(h, cudaMemcpyAsync(ne, h->d_evseries, sizeof(int) * h->series_cap * EV, cudaMemcpyDeviceToDevice,
+                                 h->stream));
+    }
+    struct {
+        double* s;
+        int* e;
+        long long c;
+    } ptrs = {ns, ne, nc};
+    static_assert(offsetof(Ctrl, evseries) == offsetof(Ctrl, series) + sizeof(double*), "layout");
+    static_assert(offsetof(Ctrl, series_cap) == offsetof(Ctrl, evseries) + sizeof(int*), "layout");
+    OD_CK(h, cudaMemcpyAsync((char*)h->B.ctrl + offsetof(Ctrl, series), &ptrs, sizeof(ptrs), cudaMemcpyHostToDevice,
+                             h->stream));
+    OD_CK(h, cudaStreamSynchronize(h->stream));
+    if (h->d_series) cudaFree(h->d_series);
+    if (h->d_evseries) cudaFree(h->d_evseries);
+    h->d_series = ns;
+    h->d_evseries = ne;
+    h->series_cap = nc;
+    return OD_OK;
+}
+
+void free_all(od_handle* h)
+{
+    for (int b = 0; b < 2; ++b) {
+        cudaFree(h->B.x[b]);
+        cudaFree(h->B.v[b]);
+        cudaFree(h->B.id[b]);
+    }
+    cudaFree(h->B.acc);
+    cudaFree(h->B.fpos);
+    cudaFree(h->B.part);
+    cudaFree(h->B.tile_status);
+    cudaFree(h->B.inj);
+    cudaFree(h->B.rem);
+    cudaFree(h->B.dpart);
+    cudaFree(h->B.ctrl);
+    cudaFree(h->d_stats);
+    cudaFree(h->d_series);
+    cudaFree(h->d_evseries);
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    for (auto& e : h->ev)
+        if (e) cudaEventDestroy(e);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+}
+
+int create_impl(const od_params* p, od_handle* h)
+{
+    int dev = 0;
+    OD_CK(h, cudaGetDevice(&dev));
+    OD_CK(h, cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev));
+    if (p->cuda_stream) {
+        h->stream = (cudaStream_t)p->cuda_stream;
+    } else {
+        OD_CK(h, cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+        h->own_stream = true;
+    }
+    derive(p, h->P, h);
+    const bool eout_on = !(p->flags & OD_F_NO_EOUT);
+    if (p->eout_coeffs) {
+        std::memcpy(h->alpha, p->eout_coeffs, sizeof(double) * 15);
+    } else if (eout_on) {
+        int rc = build_eout(h, p);
+        if (rc) return rc;
+    }
+    set_field_coeffs(h->P, h->alpha, eout_on);
+    const int N = h->P.N;
+    h->cap = std::max(N, 1);
+    h->npad_cap = ((long long)h->cap + 1023) / 1024 * 1024;
+    h->nb_cap = (h->cap + kick_block() - 1) / kick_block();
+    h->variant = -1;
+    Bufs& B = h->B;
+    B.cap = h->cap;
+    for (int b = 0; b < 2; ++b) {
+        OD_CK(h, cudaMalloc(&B.x[b], sizeof(double) * 3 * h->cap));
+        OD_CK(h, cudaMalloc(&B.v[b], sizeof(double) * 3 * h->cap));
+        OD_CK(h, cudaMalloc(&B.id[b], sizeof(unsigned long long) * h->cap));
+    }
+    OD_CK(h, cudaMalloc(&B.acc, sizeof(float4) * h->npad_cap));
+    OD_CK(h, cudaMalloc(&B.fpos, sizeof(float4) * h->npad_cap));
+    const long long ntiles = (h->cap + push_tile() - 1) / push_tile();
+    OD_CK(h, cudaMalloc(&B.tile_status, sizeof(unsigned long long) * ntiles));
+    OD_CK(h, cudaMemsetAsync(B.tile_status, 0, sizeof(unsigned long long) * ntiles, h->stream));
+    OD_CK(h, cudaMalloc(&B.inj, sizeof(Inj) * h->cap));
+    OD_CK(h, cudaMalloc(&B.rem, sizeof(Rem) * h->cap));
+    OD_CK(h, cudaMalloc(&B.dpart, sizeof(double) * h->nb_cap * MAXD * 3));
+    OD_CK(h, cudaMalloc(&B.ctrl, sizeof(Ctrl)));
+    OD_CK(h, cudaMalloc(&h->d_stats, sizeof(double) * 2 * MAXD * REC));
+    Ctrl c0;
+    std::memset(&c0, 0, sizeof(c0));
+    c0.next_id = (unsigned long long)N;
+    for (int k = 0; k < p->n_dust; ++k) c0.Q[k] = p->dust[k].q0;
+    OD_CK(h, cudaMemcpyAsync(B.ctrl, &c0, sizeof(Ctrl), cudaMemcpyHostToDevice, h->stream));
+    int rc = replan(h, N);
+    if (rc) return rc;
+    OD_LK(h, launch_init_ions(h->P, B, h->stream));
+    OD_LK(h, launch_fpos(h->P, B, 0, h->stream));
+    rc = force_eval(h);
+    if (rc) return rc;
+    rc = ensure_series(h, 1024);
+    if (rc) return rc;
+    for (auto& e : h->ev) OD_CK(h, cudaEventCreate(&e));
+    return read_error_word(h);
+}
+
+}  // namespace
+
+extern "C" {
+
+int od_create(const od_params* p, od_handle** out)
+{
+    if (!out) return fail(nullptr, OD_EINVAL, "out is NULL");
+    *out = nullptr;
+    std::string msg;
+    int rc = validate(p, msg);
+    if (rc) return fail(nullptr, rc, msg);
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return fail(nullptr, OD_ENODEV, "no CUDA device");
+    od_handle* h = new od_handle();
+    rc = create_impl(p, h);
+    if (rc) {
+        g_create_error = h->err;
+        free_all(h);
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return OD_OK;
+}
+
+int od_step(od_handle* h, int64_t n)
+{
+    if (!h || n < 0) return fail(h, OD_EINVAL, "bad handle or step count");
+    if (n == 0) return OD_OK;
+    int rc = ensure_series(h, h->host_step + n);
+    if (rc) return rc;
+    const bool direct = h->profiling || (h->P.flags & OD_F_NO_GRAPH);
+    if (!direct && !h->graph_ok) {
+        if (h->gexec) cudaGraphExecDestroy(h->gexec);
+        if (h->graph) cudaGraphDestroy(h->graph);
+        h->gexec = nullptr;
+        h->graph = nullptr;
+        OD_CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+        int lrc = launch_step(h);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+        if (lrc) return lrc;
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+        h->graph = g;
+        OD_CK(h, cudaGraphInstantiate(&h->gexec, g, 0));
+        h->graph_ok = true;
+    }
+    for (int64_t s = 0; s < n; ++s) {
+        if (direct) {
+            if (h->profiling) {
+                OD_CK(h, cudaEventRecord(h->ev[0], h->stream));
+                OD_LK(h, launch_push_scan(h->P, h->B, h->stream));
+                OD_CK(h, cudaEventRecord(h->ev[1], h->stream));
+                OD_LK(h, launch_forces(h->P, h->B, h->F, h->variant, h->stream));
+                OD_CK(h, cudaEventRecord(h->ev[2], h->stream));
+                OD_LK(h, launch_kick(h->P, h->B, h->F, 0, h->stream));
+                OD_CK(h, cudaEventRecord(h->ev[3], h->stream));
+                OD_LK(h, launch_dust(h->P, h->B, 0, h->stream));
+                OD_CK(h, cudaEventRecord(h->ev[4], h->stream));
+                OD_CK(h, cudaEventSynchronize(h->ev[4]));
+                for (int k = 0; k < 4; ++k) {
+                    float ms = 0.f;
+                    OD_CK(h, cudaEventElapsedTime(&ms, h->ev[k], h->ev[k + 1]));
+                    h->kms[k] += ms;
+                    h->klaunch[k] += 1;
+                }
+            } else {
+                rc = launch_step(h);
+                if (rc) return rc;
+            }
+        } else {
+            OD_CK(h, cudaGraphLaunch(h->gexec, h->stream));
+        }
+    }
+    h->host_step += n;
+    return read_error_word(h);
+}
+
+void od_destroy(od_handle* h)
+{
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    free_all(h);
+    delete h;
+}
+
+int od_dust_terms(od_handle* h, double* mean, double* se)
+{
+    if (!h) return fail(h, OD_EINVAL, "bad handle");
+    OD_LK(h, launch_stats(h->P, h->B, h->d_stats, h->stream));
+    double buf[2 * MAXD * REC];
+    OD_CK(h, cudaMemcpyAsync(buf, h->d_stats, sizeof(buf), cudaMemcpyDeviceToHost, h->stream));
+    OD_CK(h, cudaStreamSynchronize(h->stream));
+    const int n = h->P.D * REC;
+    if (mean) std::memcpy(mean, buf, sizeof(double) * n);
+    if (se) std::memcpy(se, buf + MAXD * REC, sizeof(double) * n);
+    return OD_OK;
+}
+
+int od_dust_state(od_handle* h, double* q, double* F)
+{
+    double mean[MAXD * REC];
+    int rc = od_dust_terms(h, mean, nullptr);
+    if (rc) return rc;
+    for (int k = 0; k < h->P.D; ++k) {
+        const double* r = mean + k * REC;
+        if (q) q[k] = r[0];
+        if (F)
+            for (int c = 0; c < 3; ++c) F[3 * k + c] = r[1 + c] + r[4 + c] + r[7 + c] + r[10 + c];
+    }
+    return OD_OK;
+}
+
+int od_series(od_handle* h, int64_t first, int64_t count, double* rec, int32_t* ev)
+{
+    if (!h) return fail(h, OD_EINVAL, "bad handle");
+    if (first < 1 || count < 0 || first + count - 1 > h->host_step || first + count - 1 > h->series_cap)
+        return fail(h, OD_EINVAL, "series range outside the steps taken");
+    if (count == 0) return OD_OK;
+    const int D = h->P.D;
+    if (rec) {
+        std::vector<double> tmp((size_t)count * MAXD * REC);
+        OD_CK(h, cudaMemcpyAsync(tmp.data(), h->d_series + (first - 1) * MAXD * REC, sizeof(double) * tmp.size(),
+                                 cudaMemcpyDeviceToHost, h->stream));
+        OD_CK(h, cudaStreamSynchronize(h->stream));
+        for (int64_t t = 0; t < count; ++t)
+            std::memcpy(rec + (t * D) * REC, tmp.data() + t * MAXD * REC, sizeof(double) * D * REC);
+    }
+    if (ev) {
+        OD_CK(h, cudaMemcpyAsync(ev, h->d_evseries + (first - 1) * EV, sizeof(int) * count * EV,
+                                 cudaMemcpyDeviceToHost, h->stream));
+        OD_CK(h, cudaStreamSynchronize(h->stream));
+    }
+    return OD_OK;
+}
+
+int od_counters(od_handle* h, int64_t* out)
+{
+    if (!h || !out) return fail(h, OD_EINVAL, "bad argument");
+    OD_CK(h, cudaMemcpyAsync(out, (char*)h->B.ctrl + offsetof(Ctrl, counters), sizeof(long long) * OD_NCOUNT,
+                             cudaMemcpyDeviceToHost, h->stream));
+    OD_CK(h, cudaStreamSynchronize(h->stream));
+    out[13] = h->host_step;
+    out[14] = h->P.N;
+    return OD_OK;
+}
+
+int od_dust_now(od_handle* h, double* q, double* f_orbit)
+{
+    if (!h) return fail(h, OD_EINVAL, "bad handle");
+    Ctrl c;
+    OD_CK(h, cudaMemcpyAsync(&c, h->B.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
+    OD_CK(h, cudaStreamSynchronize(h->stream));
+    for (int k = 0; k < h->P.D; ++k) {
+        if (q) q[k] = c.Q[k];
+        if (f_orbit)
+            for (int j = 0; j < 3; ++j) f_orbit[3 * k + j] = c.f_orbit[k][j];
+    }
+    return OD_OK;
+}
+
+int64_t od_get_ions(od_handle* h, double* x, double* v, double* a, uint64_t* id, int64_t cap)
+{
+    if (!h) return fail(h, OD_EINVAL, "bad handle");
+    const long long N = h->P.N;
+    if ((x || v || a || id) && cap < N) return fail(h, OD_EINVAL, "host arrays too small");
+    const int buf = (int)(h->host_step & 1);
+    std::vector<double> tmp(3 * (size_t)N);
+    auto inter = [&](const double* d, double* o) -> int {
+        for (int c = 0; c < 3; ++c)
+            OD_CK(h, cudaMemcpyAsync(tmp.data() + c * N, d + c * h->cap, sizeof(double) * N, cudaMemcpyDeviceToHost,
+                                     h->stream));
+        OD_CK(h, cudaStreamSynchronize(h->stream));
+        for (long long i = 0; i < N; ++i)
+            for (int c = 0; c < 3; ++c) o[3 * i + c] = tmp[c * N + i];
+        return OD_OK;
+    };
+    if (N > 0) {
+        int rc;
+        if (x && (rc = inter(h->B.x[buf], x))) return rc;
+        if (v && (rc = inter(h->B.v[buf], v))) return rc;
+        if (a) {
+            std::vector<float4> ta(N);
+            OD_CK(h, cudaMemcpyAsync(ta.data(), h->B.acc, sizeof(float4) * N, cudaMemcpyDeviceToHost, h->stream));
+            OD_CK(h, cudaStreamSynchronize(h->stream));
+            for (long long i = 0; i < N; ++i) {
+                a[3 * i] = ta[i].x;
+                a[3 * i + 1] = ta[i].y;
+                a[3 * i + 2] = ta[i].z;
+            }
+        }
+        if (id) {
+            OD_CK(h, cudaMemcpyAsync(id, h->B.id[buf], sizeof(uint64_t) * N, cudaMemcpyDeviceToHost, h->stream));
+            OD_CK(h, cudaStreamSynchronize(h->stream));
+        }
+    }
+    return N;
+}
+
+int od_set_ions(od_handle* h, const double* x, const double* v, const double* a, const uint64_t* id, int64_t n,
+                uint64_t next_id)
+{
+    if (!h || n < 0 || (n > 0 && (!x || !v || !id))) return fail(h, OD_EINVAL, "bad argument");
+    if (n > h->cap) return fail(h, OD_EOVERFLOW, "more ions than the handle's capacity");
+    const int buf = (int)(h->host_step & 1);
+    std::vector<double> tmp(3 * (size_t)n);
+    auto upload = [&](const double* src, double* d) -> int {
+        for (int64_t i = 0; i < n; ++i)
+            for (int c = 0; c < 3; ++c) tmp[c * n + i] = src[3 * i + c];
+        for (int c = 0; c < 3; ++c)
+            OD_CK(h, cudaMemcpyAsync(d + c * h->cap, tmp.data() + c * n, sizeof(double) * n, cudaMemcpyHostToDevice,
+                                     h->stream));
+        OD_CK(h, cudaStreamSynchronize(h->stream));
+        return OD_OK;
+    };
+    int rc;
+    if (n > 0) {
+        if ((rc = upload(x, h->B.x[buf]))) return rc;
+        if ((rc = upload(v, h->B.v[buf]))) return rc;
+        OD_CK(h, cudaMemcpyAsync(h->B.id[buf], id, sizeof(uint64_t) * n, cudaMemcpyHostToDevice, h->stream));
+    }
+    unsigned long long nid = next_id;
+    OD_CK(h, cudaMemcpyAsync((char*)h->B.ctrl + offsetof(Ctrl, next_id), &nid, sizeof(nid), cudaMemcpyHostToDevice,
+                             h->stream));
+    const int variant = h->variant;
+    if ((rc = replan(h, (int)n))) return rc;
+    (void)variant;
+    h->graph_ok = false;
+    OD_LK(h, launch_fpos(h->P, h->B, buf, h->stream));
+    if (a) {
+        std::vector<float4> ta(std::max<int64_t>(n, 1));
+        for (int64_t i = 0; i < n; ++i) ta[i] = make_float4((float)a[3 * i], (float)a[3 * i + 1], (float)a[3 * i + 2], 0.f);
+        if (n > 0)
+            OD_CK(h, cudaMemcpyAsync(h->B.acc, ta.data(), sizeof(float4) * n, cudaMemcpyHostToDevice, h->stream));
+        OD_CK(h, cudaStreamSynchronize(h->stream));
+    } else {
+        if ((rc = force_eval(h))) return rc;
+    }
+    return read_error_word(h);
+}
+
+int od_info(od_handle* h, double* out)
+{
+    if (!h || !out) return fail(h, OD_EINVAL, "bad argument");
+    for (int i = 0; i < 32; ++i) out[i] = h->info[i];
+    out[14] = h->P.N;
+    for (int t = 0; t < 15; ++t) out[15 + t] = h->alpha[t];
+    out[30] = (double)h->cap;
+    out[31] = h->sms;
+    return OD_OK;
+}
+
+int od_set_profiling(od_handle* h, int on)
+{
+    if (!h) return fail(h, OD_EINVAL, "bad handle");
+    h->profiling = on != 0;
+    for (int k = 0; k < 4; ++k) {
+        h->kms[k] = 0.0;
+        h->klaunch[k] = 0;
+    }
+    return OD_OK;
+}
+
+int od_kernel_times(od_handle* h, double* ms, int64_t* launches)
+{
+    if (!h) return fail(h, OD_EINVAL, "bad handle");
+    for (int k = 0; k < 4; ++k) {
+        if (ms) ms[k] = h->kms[k];
+        if (launches) launches[k] = h->klaunch[k];
+    }
+    return OD_OK;
+}
+
+const char* od_last_error(const od_handle* h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,135 @@
+// Internal types of the GB300 ion-flow-around-dust library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "opendust.h"
+
+namespace od {
+
+constexpr int MAXD = OD_MAX_DUST;
+constexpr int REC = OD_REC;
+constexpr int EV = OD_EV;
+
+// error bits of the device error word
+constexpr int ERR_NAN = 1;
+constexpr int ERR_TIMEOUT = 2;
+constexpr int ERR_OVERFLOW = 4;
+constexpr int ERR_PLACE = 8;
+
+// Philox streams (fourth counter word): the same layout on host and device.
+enum : uint32_t { ST_INIT_POS = 0, ST_INIT_VEL = 1, ST_COLL = 2, ST_COLL_VEL = 3, ST_INJ_A = 4, ST_INJ_B = 5 };
+
+// Device-resident control block: everything a step changes lives here, so a
+// captured graph of one step can be replayed without host involvement.
+struct Ctrl {
+    long long step;               // steps completed
+    unsigned long long next_id;   // id of the next injected ion
+    int err;                      // ERR_* bits
+    unsigned tile_counter;        // dynamic tile ids of the scan kernel
+    unsigned done_counter;        // finished tiles of the scan kernel
+    int removed_total;            // ions removed in the current step
+    int ev_step[EV];              // this step's event counts
+    int pad0;
+    double Q[MAXD];               // grain charges
+    double f_orbit[MAXD][3];      // Eq. 1 force at the last force evaluation
+    double wsum[MAXD][REC];       // window sums of the records
+    long long wcount;             // records in the window
+    long long counters[OD_NCOUNT];
+    double* series;               // [cap][MAXD][REC]
+    int* evseries;                // [cap][EV]
+    long long series_cap;
+};
+
+// Injected-ion staging (rank order) and removed-ion records (rank order)
+struct Inj {
+    double x, y, z, vx, vy, vz;
+    unsigned long long id;
+    int face;
+    int pad;
+};
+struct Rem {
+    double vx, vy, vz;
+    int cls;  // -1 outflow, k >= 0 absorbed by grain k
+    int pad;
+};
+
+// Physical constants and run parameters, passed by value to every kernel.
+struct Phys {
+    int N, n_pad, D, flags;
+    double dt, R, H, hz, R2;
+    double qm;       // Z e / m_i
+    double kdi;      // Z e / (4 pi eps0 m_i): ion acceleration from a grain of charge Q
+    double korb;     // q / (4 pi eps0): Eq. 1 prefactor per unit grain charge
+    double lam_inv;  // 1 / lambda_De
+    double E;        // driving field
+    double m, q;     // superion mass and charge
+    double sig, sig_n, u;
+    float Ls_inv;    // log2(e) / lambda_De: scaled coordinates for the pair kernel
+    float k_ii;      // q^2 / (4 pi eps0 m Ls^2), Ls = lambda_De / log2(e)
+    uint32_t key0, key1;
+    unsigned long long Tb, Tbt, Tcoll;
+    double gx[MAXD], gy[MAXD], gz[MAXD], ga[MAXD], ga2[MAXD];
+    // E_out = (-x G, -y G, -z K), G and K polynomials in r^2, z^2 (10 terms each)
+    double Gc[10], Kc[10];
+    int Gp[10], Gq[10], Kp[10], Kq[10];
+    int eout;
+    int charge_model;
+    long long avg_start;
+    double Ie0;      // OML electron flux at zero potential per unit area, 1/(m^2 s)
+    double e_over_kTe;
+    double inv4pieps0;
+};
+
+// Device buffers. Ion state is double-buffered (compaction writes the other copy).
+struct Bufs {
+    double* x[2];  // [3][cap] SoA: x, y, z
+    double* v[2];  // [3][cap]
+    unsigned long long* id[2];
+    float4* acc;   // accelerations of the current order
+    float4* fpos;  // scaled positions for the pair kernel, padded with far-away dummies
+    float4* part;  // pair-kernel partial sums [W][n_pad]
+    unsigned long long* tile_status;
+    Inj* inj;
+    Rem* rem;
+    double* dpart; // grain partial sums [nb][MAXD][3]
+    Ctrl* ctrl;
+    long long cap;
+};
+
+// Balanced static partition of the all-pairs work into (i-tile, j-chunk) units.
+struct ForceArgs {
+    int n_pad;   // multiple of TI
+    int TI;      // targets per tile = BT * IPT
+    int JC;      // sources per chunk, multiple of BT
+    int JS;      // chunks per tile
+    int G;       // persistent blocks
+    int W;       // partial slots
+    long long U; // units = n_itiles * JS
+};
+
+// host launchers (od_kernels.cu)
+int launch_init_ions(const Phys& P, const Bufs& B, cudaStream_t s);
+int launch_fpos(const Phys& P, const Bufs& B, int buf, cudaStream_t s);
+int launch_pad(const Phys& P, const Bufs& B, cudaStream_t s);
+int launch_push_scan(const Phys& P, const Bufs& B, cudaStream_t s);
+int launch_forces(const Phys& P, const Bufs& B, const ForceArgs& F, int variant, cudaStream_t s);
+int launch_kick(const Phys& P, const Bufs& B, const ForceArgs& F, int mode, cudaStream_t s);
+int launch_dust(const Phys& P, const Bufs& B, int mode, cudaStream_t s);
+int launch_stats(const Phys& P, const Bufs& B, double* mean_se, cudaStream_t s);
+int launch_eout_grid(double R, double H, double lam, int nx, int nz, int nq, const double* gl_x,
+                     const double* gl_w, double* out, cudaStream_t s);
+
+// pair-kernel variants: (threads per block, targets per thread)
+struct ForceVariant {
+    int BT, IPT;
+};
+int num_force_variants();
+ForceVariant force_variant(int v);
+int force_blocks_per_sm(int variant);
+
+int push_tile();  // ions per scan tile
+int kick_block(); // threads per block of the kick kernel
+
+}  // namespace od

@@ -1,0 +1,59 @@
+"""CPU-side checks of the C ABI (no device work): the library builds and loads,
+exports every function include/opendust.h declares, the ctypes structures match the
+header's layout, and invalid parameters are rejected before any CUDA call."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2205_06557_gb300 as od
+from paper_2205_06557_gb300 import build
+from paper_2205_06557_gb300 import workloads as W
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "opendust.h")
+
+
+@pytest.fixture(scope="module")
+def L():
+    build.build()
+    return od.lib()
+
+
+def test_exports_every_declared_function(L):
+    names = set(re.findall(r"^\s*(?:int|int64_t|void|const char\*)\s+(od_[a-z_]+)\s*\(", open(HEADER).read(), re.M))
+    assert {"od_create", "od_step", "od_dust_state", "od_destroy"} <= names
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing
+
+
+def test_struct_layout_matches_header():
+    # 13 doubles, int64, 2 x int32, pointer, uint64, int64, pointer, 2 x int32, pointer
+    assert ctypes.sizeof(od.od_params) == 13 * 8 + 8 + 8 + 8 + 8 + 8 + 8 + 8 + 8
+    assert ctypes.sizeof(od.od_dust) == 40
+    assert od.od_params.cuda_stream.offset == ctypes.sizeof(od.od_params) - 8
+
+
+def _rc(L, p):
+    s, keep = od.make_params(p)
+    h = ctypes.c_void_p()
+    return L.od_create(ctypes.byref(s), ctypes.byref(h)), od.od_last_error()
+
+
+@pytest.mark.parametrize("change", [
+    dict(R=-1.0), dict(dt=0.0), dict(T_e=float("nan")), dict(mach=1.0, E_ext=100.0), dict(mach=0.0, E_ext=100.0, nu=0.0),
+    dict(dust=[dict(x=1.95e-4, y=0.0, z=0.0, a=1e-5, q0=0.0)]),
+    dict(dust=[dict(x=0.0, y=0.0, z=0.0, a=2e-5, q0=0.0)] * 9),
+    dict(n_ions=-3), dict(weight=0.0),
+])
+def test_invalid_parameters_rejected_on_host(L, change):
+    p = W.tiny()
+    p.update(change)
+    rc, msg = _rc(L, p)
+    assert rc == -1 and msg
+
+
+def test_null_arguments(L):
+    assert L.od_create(None, None) == -1
+    assert L.od_step(None, 1) == -1
+    L.od_destroy(None)
