@@ -37,7 +37,7 @@ PAIRS_PER_CLK_SM = 8.0  # FP32 pipe (16 FP32 ops / pair at 128 lanes) and SFU (2
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="scale", choices=["scale", "tiny", "chain"])
