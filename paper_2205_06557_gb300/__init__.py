@@ -96,6 +96,8 @@ def lib():
         L.od_kernel_times.argtypes = [vp, vp, vp]
         L.od_last_error.argtypes = [vp]
         L.od_last_error.restype = ctypes.c_char_p
+        L.od_pair_accel_static.argtypes = [vp, i64, ctypes.c_double, ctypes.c_double, vp, vp]
+        L.od_pair_accel_static.restype = ctypes.c_int
         for name in ("od_create", "od_step", "od_dust_state", "od_dust_terms", "od_series", "od_counters",
                      "od_dust_now", "od_set_ions", "od_info", "od_set_profiling", "od_kernel_times"):
             getattr(L, name).restype = ctypes.c_int
@@ -242,6 +244,16 @@ def od_kernel_times(h):
 def od_last_error(h=None):
     m = lib().od_last_error(h)
     return m.decode() if m else ""
+
+
+STATIC_MAX_IONS = 32768
+
+
+def od_pair_accel_static(x_dev, n, lambda_De, k, a_dev, stream=None):
+    """Pair accelerations without device allocation. x_dev, a_dev are device
+    addresses (ints) of [n][3] FP64 positions and [n][3] FP32 accelerations."""
+    return _check(lib().od_pair_accel_static(ctypes.c_void_p(x_dev), int(n), float(lambda_De), float(k),
+                                             ctypes.c_void_p(a_dev), ctypes.c_void_p(stream) if stream else None))
 
 
 class Run:

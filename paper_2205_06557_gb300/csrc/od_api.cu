@@ -120,6 +120,8 @@ bool lsq_mgs(int m, int n, std::vector<double> A, std::vector<double> b, double*
 
 }  // namespace
 
+void od::set_global_error(const std::string& msg) { g_create_error = msg; }
+
 struct od_handle {
     Phys P{};
     Bufs B{};

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "opendust.h"
 
 namespace od {
@@ -128,6 +130,9 @@ struct ForceVariant {
 int num_force_variants();
 ForceVariant force_variant(int v);
 int force_blocks_per_sm(int variant);
+
+// message returned by od_last_error(NULL) for calls without a handle (od_api.cu)
+void set_global_error(const std::string& msg);
 
 int push_tile();  // ions per scan tile
 int kick_block(); // threads per block of the kick kernel

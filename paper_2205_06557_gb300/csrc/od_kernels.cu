@@ -10,7 +10,11 @@
 //   k_dust       grain tail: Eq. 1-4 terms, charge update, records, time averages
 // Every kernel reads the step number from device memory, so a captured graph of one
 // step replays without the host.
+#include <algorithm>
+#include <cmath>
 #include <cstdio>
+#include <mutex>
+#include <string>
 
 #include "od_internal.h"
 
@@ -944,3 +948,121 @@ int launch_eout_grid(double R, double H, double lam, int nx, int nz, int nq, con
 }
 
 }  // namespace od
+
+// ---------------------------------------------- no-allocation pair forces
+// A variant of the pair-force computation for callers that cannot allocate device
+// memory.  Its scratch (scaled positions and the per-chunk partial sums) lives in
+// one file-scope device array of fixed size that every GPU loading this library
+// holds until the process exits.  Host code only sees a stand-in for the array's
+// name, so the device address is looked up once per device with
+// cudaGetSymbolAddress and passed to the kernels.
+namespace od {
+namespace {
+constexpr int kStaticBT = 128, kStaticIPT = 2, kStaticTI = kStaticBT * kStaticIPT;
+constexpr int kStaticSlots = 8;  // source chunks per target tile
+constexpr long long kStaticFloat4 = (long long)OD_STATIC_MAX_IONS * (1 + kStaticSlots);
+static_assert(OD_STATIC_MAX_IONS % kStaticTI == 0, "capacity must be a whole number of tiles");
+}  // namespace
+
+static __device__ __align__(256) float4 g_static_scratch[kStaticFloat4];
+
+__global__ void k_static_scale(const double* __restrict__ x, int n, int n_pad, double ls_inv, float4* __restrict__ fpos)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_pad) return;
+    if (i < n) {
+        fpos[i] = make_float4((float)(x[3 * i] * ls_inv), (float)(x[3 * i + 1] * ls_inv), (float)(x[3 * i + 2] * ls_inv),
+                              0.0f);
+    } else {
+        const float far = 3.0e4f + 7.0f * (float)(i - n);
+        fpos[i] = make_float4(far, far, far, 0.0f);
+    }
+}
+
+__global__ void k_static_reduce(const float4* __restrict__ part, int n, int n_pad, int slots, float kscale,
+                                float* __restrict__ a)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float ax = 0.f, ay = 0.f, az = 0.f;
+    for (int s = 0; s < slots; ++s) {
+        const float4 p = part[(long long)s * n_pad + i];
+        ax += p.x;
+        ay += p.y;
+        az += p.z;
+    }
+    a[3 * i] = -kscale * ax;
+    a[3 * i + 1] = -kscale * ay;
+    a[3 * i + 2] = -kscale * az;
+}
+
+static float4* static_scratch_address(int dev, int* rc)
+{
+    static std::mutex mu;
+    static float4* addr[256] = {nullptr};
+    *rc = OD_OK;
+    if (dev < 0 || dev >= 256) {
+        *rc = OD_EINVAL;
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess || !p) {
+            *rc = OD_ECUDA;
+            set_global_error(std::string("cudaGetSymbolAddress of the static scratch failed: ") + cudaGetErrorString(e));
+            return nullptr;
+        }
+        addr[dev] = (float4*)p;
+    }
+    return addr[dev];
+}
+
+}  // namespace od
+
+extern "C" int od_pair_accel_static(const double* x, int64_t n, double lambda_De, double k, float* a, void* stream)
+{
+    using namespace od;
+    if (n < 0 || n > OD_STATIC_MAX_IONS) {
+        set_global_error("od_pair_accel_static: n must be in 0.." + std::to_string(OD_STATIC_MAX_IONS));
+        return OD_EINVAL;
+    }
+    if (!(lambda_De > 0.0) || !std::isfinite(lambda_De) || !std::isfinite(k) || (n > 0 && (!x || !a))) {
+        set_global_error("od_pair_accel_static: lambda_De must be finite and > 0, k finite, x and a non-NULL");
+        return OD_EINVAL;
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        set_global_error("od_pair_accel_static: no current CUDA device");
+        return OD_ENODEV;
+    }
+    int rc = OD_OK;
+    float4* base = static_scratch_address(dev, &rc);
+    if (!base) return rc;
+    if (n == 0) return OD_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const double ls_inv = 1.4426950408889634 / lambda_De;  // log2(e) / lambda_De
+    ForceArgs F{};
+    F.TI = kStaticTI;
+    F.n_pad = (int)((n + kStaticTI - 1) / kStaticTI * kStaticTI);
+    const int n_it = F.n_pad / kStaticTI;
+    int js = std::min(kStaticSlots, F.n_pad / kStaticBT);
+    F.JC = ((F.n_pad + js - 1) / js + kStaticBT - 1) / kStaticBT * kStaticBT;
+    F.JS = (F.n_pad + F.JC - 1) / F.JC;
+    F.U = (long long)n_it * F.JS;
+    F.G = (int)F.U;  // one unit per block: the partial slot of a block is its chunk index
+    F.W = F.JS;
+    float4* fpos = base;
+    float4* part = base + OD_STATIC_MAX_IONS;
+    k_static_scale<<<(F.n_pad + 255) / 256, 256, 0, s>>>(x, (int)n, F.n_pad, ls_inv, fpos);
+    k_forces<kStaticBT, kStaticIPT><<<F.G, kStaticBT, 0, s>>>(fpos, part, F);
+    const float kscale = (float)(k * ls_inv * ls_inv);
+    k_static_reduce<<<(int)((n + 255) / 256), 256, 0, s>>>(part, (int)n, F.n_pad, F.JS, kscale, a);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_global_error(std::string("od_pair_accel_static: launch failed: ") + cudaGetErrorString(e));
+        return OD_ECUDA;
+    }
+    return OD_OK;
+}
