@@ -154,6 +154,18 @@ int od_info(od_handle* h, double* out);
 int od_set_profiling(od_handle* h, int on);
 int od_kernel_times(od_handle* h, double* ms, int64_t* launches);
 
+/* Pair-kernel autotuner (the all-pairs force evaluation of Sec. 5 is the hot spot).
+ * od_tune times every kernel variant (threads per block x targets per thread) at four
+ * work granularities (4, 8, 16, 32 units per persistent block) on the run's current
+ * ions, reps launches each, keeps the fastest and writes the average ms per launch
+ * to ms[n_variants * 4] (host, may be NULL; row = variant, column = granularity).
+ * od_set_force_config applies a known choice (e.g. from a cache) and
+ * od_get_force_config reports the current one and the number of variants.  The ion
+ * state is not changed; call between steps. */
+int od_tune(od_handle* h, int reps, double* ms, int* best_variant, int* best_units_per_block);
+int od_set_force_config(od_handle* h, int variant, int units_per_block);
+int od_get_force_config(od_handle* h, int* variant, int* units_per_block, int* n_variants);
+
 /* Text of the last error on h, or of the last failed call without a handle (od_create,
  * od_pair_accel_static) when h is NULL. */
 const char* od_last_error(const od_handle* h);

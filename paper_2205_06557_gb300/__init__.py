@@ -98,6 +98,11 @@ def lib():
         L.od_last_error.restype = ctypes.c_char_p
         L.od_pair_accel_static.argtypes = [vp, i64, ctypes.c_double, ctypes.c_double, vp, vp]
         L.od_pair_accel_static.restype = ctypes.c_int
+        L.od_tune.argtypes = [vp, ctypes.c_int, vp, vp, vp]
+        L.od_set_force_config.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+        L.od_get_force_config.argtypes = [vp, vp, vp, vp]
+        for name in ("od_tune", "od_set_force_config", "od_get_force_config"):
+            getattr(L, name).restype = ctypes.c_int
         for name in ("od_create", "od_step", "od_dust_state", "od_dust_terms", "od_series", "od_counters",
                      "od_dust_now", "od_set_ions", "od_info", "od_set_profiling", "od_kernel_times"):
             getattr(L, name).restype = ctypes.c_int
@@ -244,6 +249,56 @@ def od_kernel_times(h):
 def od_last_error(h=None):
     m = lib().od_last_error(h)
     return m.decode() if m else ""
+
+
+def od_get_force_config(h):
+    v, g, nv = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().od_get_force_config(h, ctypes.byref(v), ctypes.byref(g), ctypes.byref(nv)), h)
+    return v.value, g.value, nv.value
+
+
+def od_set_force_config(h, variant, units_per_block):
+    return _check(lib().od_set_force_config(h, int(variant), int(units_per_block)), h)
+
+
+def od_tune(h, reps=3):
+    """time every pair-kernel configuration; returns (ms[n_variants, 4], best_variant, best_upb)"""
+    nv = od_get_force_config(h)[2]
+    ms = np.zeros((nv, 4))
+    bv, bg = ctypes.c_int(), ctypes.c_int()
+    _check(lib().od_tune(h, int(reps), _ptr(ms), ctypes.byref(bv), ctypes.byref(bg)), h)
+    return ms, bv.value, bg.value
+
+
+def _tune_cache_path():
+    return os.environ.get("OPENDUST_TUNE_CACHE",
+                          os.path.join(os.path.expanduser("~"), ".cache", "opendust_gb300", "tune.json"))
+
+
+def tune_cached(h, key, reps=3, path=None):
+    """Apply the cached pair-kernel choice for `key` (e.g. device name and ion count),
+    or run od_tune and store its choice in the JSON cache."""
+    import json
+
+    path = path or _tune_cache_path()
+    try:
+        cache = json.load(open(path))
+    except (OSError, ValueError):
+        cache = {}
+    if key in cache:
+        v, g = cache[key]
+        od_set_force_config(h, v, g)
+        return v, g, None
+    ms, v, g = od_tune(h, reps)
+    cache[key] = [v, g]
+    try:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        tmp = path + ".tmp%d" % os.getpid()
+        json.dump(cache, open(tmp, "w"), indent=1)
+        os.replace(tmp, path)
+    except OSError:
+        pass
+    return v, g, ms
 
 
 STATIC_MAX_IONS = 32768

@@ -127,6 +127,7 @@ struct od_handle {
     Bufs B{};
     ForceArgs F{};
     int variant = 0;
+    int upb = 8;  // pair-kernel work units per persistent block
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     cudaGraph_t graph = nullptr;
@@ -417,7 +418,7 @@ int replan(od_handle* h, int N)
 {
     h->P.N = N;
     if (h->variant < 0 || h->variant >= num_force_variants()) h->variant = default_variant(N);
-    h->F = plan_forces(N, h->variant, h->sms, 8);
+    h->F = plan_forces(N, h->variant, h->sms, h->upb);
     h->P.n_pad = h->F.n_pad;
     if (h->F.n_pad > h->npad_cap) return fail(h, OD_EOVERFLOW, "padded ion count exceeds the buffer");
     return ensure_part(h);
@@ -846,5 +847,81 @@ int od_kernel_times(od_handle* h, double* ms, int64_t* launches)
 }
 
 const char* od_last_error(const od_handle* h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+static const int kTuneGrains[4] = {4, 8, 16, 32};
+
+static int apply_force_config(od_handle* h, int variant, int upb)
+{
+    h->variant = variant;
+    h->upb = upb;
+    int rc = replan(h, h->P.N);
+    if (rc) return rc;
+    h->graph_ok = false;
+    // the padded length may have grown: rewrite positions and far-away dummies
+    OD_LK(h, launch_fpos(h->P, h->B, (int)(h->host_step & 1), h->stream));
+    return OD_OK;
+}
+
+int od_set_force_config(od_handle* h, int variant, int units_per_block)
+{
+    if (!h || variant < 0 || variant >= num_force_variants() || units_per_block < 1 || units_per_block > 1024)
+        return fail(h, OD_EINVAL, "bad force configuration");
+    int rc = apply_force_config(h, variant, units_per_block);
+    if (rc) return rc;
+    OD_CK(h, cudaStreamSynchronize(h->stream));
+    return OD_OK;
+}
+
+int od_tune(od_handle* h, int reps, double* ms, int* best_variant, int* best_upb)
+{
+    if (!h || reps < 1) return fail(h, OD_EINVAL, "bad handle or repetition count");
+    const int nv = num_force_variants();
+    if (ms)
+        for (int i = 0; i < nv * 4; ++i) ms[i] = -1.0;
+    if (h->P.N == 0 || (h->P.flags & OD_F_NO_IONION)) {
+        if (best_variant) *best_variant = h->variant;
+        if (best_upb) *best_upb = h->upb;
+        return OD_OK;
+    }
+    double best = 1e300;
+    int bv = h->variant, bg = h->upb;
+    for (int v = 0; v < nv; ++v)
+        for (int g = 0; g < 4; ++g) {
+            int rc = apply_force_config(h, v, kTuneGrains[g]);
+            if (rc) return rc;
+            OD_LK(h, launch_forces(h->P, h->B, h->F, h->variant, h->stream));
+            OD_CK(h, cudaEventRecord(h->ev[0], h->stream));
+            for (int r = 0; r < reps; ++r) OD_LK(h, launch_forces(h->P, h->B, h->F, h->variant, h->stream));
+            OD_CK(h, cudaEventRecord(h->ev[1], h->stream));
+            OD_CK(h, cudaEventSynchronize(h->ev[1]));
+            float t = 0.f;
+            OD_CK(h, cudaEventElapsedTime(&t, h->ev[0], h->ev[1]));
+            const double avg = t / reps;
+            if (ms) ms[v * 4 + g] = avg;
+            if (avg < best) {
+                best = avg;
+                bv = v;
+                bg = kTuneGrains[g];
+            }
+        }
+    int rc = apply_force_config(h, bv, bg);
+    if (rc) return rc;
+    // the last force evaluation's partial sums belong to the configuration just left:
+    // recompute them for the chosen one so the next kick reads a consistent layout
+    OD_LK(h, launch_forces(h->P, h->B, h->F, h->variant, h->stream));
+    OD_CK(h, cudaStreamSynchronize(h->stream));
+    if (best_variant) *best_variant = bv;
+    if (best_upb) *best_upb = bg;
+    return read_error_word(h);
+}
+
+int od_get_force_config(od_handle* h, int* variant, int* units_per_block, int* n_variants)
+{
+    if (!h) return fail(h, OD_EINVAL, "bad handle");
+    if (variant) *variant = h->variant;
+    if (units_per_block) *units_per_block = h->upb;
+    if (n_variants) *n_variants = num_force_variants();
+    return OD_OK;
+}
 
 }  // extern "C"

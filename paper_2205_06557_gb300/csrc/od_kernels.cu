@@ -876,27 +876,27 @@ int launch_push_scan(const Phys& P, const Bufs& B, cudaStream_t s)
     return ck(cudaGetLastError());
 }
 
-static const ForceVariant kVariants[] = {{64, 1}, {64, 2}, {128, 2}, {128, 4}, {256, 2}, {256, 4}};
+// pair-kernel variants (threads per block, targets per thread); targets per tile
+// BT * IPT never exceeds 1024, the padding granularity of the position buffer
+#define OD_FORCE_VARIANTS(X) X(64, 1) X(64, 2) X(128, 2) X(128, 4) X(256, 2) X(256, 4) X(128, 8) X(64, 8)
+
+static const ForceVariant kVariants[] = {
+#define OD_V(bt, ipt) {bt, ipt},
+    OD_FORCE_VARIANTS(OD_V)
+#undef OD_V
+};
 
 int num_force_variants() { return (int)(sizeof(kVariants) / sizeof(kVariants[0])); }
 ForceVariant force_variant(int v) { return kVariants[v]; }
 
-template <int BT, int IPT>
-static void* force_fn()
-{
-    return (void*)k_forces<BT, IPT>;
-}
-
 static void* variant_fn(int v)
 {
-    switch (v) {
-    case 0: return force_fn<64, 1>();
-    case 1: return force_fn<64, 2>();
-    case 2: return force_fn<128, 2>();
-    case 3: return force_fn<128, 4>();
-    case 4: return force_fn<256, 2>();
-    default: return force_fn<256, 4>();
-    }
+    static void* const fns[] = {
+#define OD_V(bt, ipt) (void*)k_forces<bt, ipt>,
+        OD_FORCE_VARIANTS(OD_V)
+#undef OD_V
+    };
+    return fns[v];
 }
 
 int force_blocks_per_sm(int v)
@@ -909,15 +909,15 @@ int force_blocks_per_sm(int v)
 int launch_forces(const Phys& P, const Bufs& B, const ForceArgs& F, int v, cudaStream_t s)
 {
     if (P.N == 0 || (P.flags & OD_F_NO_IONION) || F.G == 0) return 0;
-    switch (v) {
-    case 0: k_forces<64, 1><<<F.G, 64, 0, s>>>(B.fpos, B.part, F); break;
-    case 1: k_forces<64, 2><<<F.G, 64, 0, s>>>(B.fpos, B.part, F); break;
-    case 2: k_forces<128, 2><<<F.G, 128, 0, s>>>(B.fpos, B.part, F); break;
-    case 3: k_forces<128, 4><<<F.G, 128, 0, s>>>(B.fpos, B.part, F); break;
-    case 4: k_forces<256, 2><<<F.G, 256, 0, s>>>(B.fpos, B.part, F); break;
-    default: k_forces<256, 4><<<F.G, 256, 0, s>>>(B.fpos, B.part, F); break;
+    int idx = 0;
+#define OD_V(bt, ipt)                                                \
+    if (v == idx++) {                                                \
+        k_forces<bt, ipt><<<F.G, bt, 0, s>>>(B.fpos, B.part, F);     \
+        return ck(cudaGetLastError());                               \
     }
-    return ck(cudaGetLastError());
+    OD_FORCE_VARIANTS(OD_V)
+#undef OD_V
+    return (int)cudaErrorInvalidValue;
 }
 
 int launch_kick(const Phys& P, const Bufs& B, const ForceArgs& F, int mode, cudaStream_t s)

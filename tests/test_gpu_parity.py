@@ -258,3 +258,20 @@ def test_restart_round_trip_is_exact():
     xa, va, _, ia = a_run.get_ions()
     xb, vb, _, ib = b_run.get_ions()
     assert np.array_equal(ia, ib) and np.array_equal(xa, xb) and np.array_equal(va, vb)
+
+
+def test_tuned_configuration_keeps_results():
+    p = W.tiny()
+    ref = od.Run(p)
+    tuned = od.Run(p)
+    ms, v, g = od.od_tune(tuned.h, reps=1)
+    assert ms[v, [4, 8, 16, 32].index(g)] == ms[ms > 0].min()
+    assert od.od_get_force_config(tuned.h)[:2] == (v, g)
+    ref.step(20)
+    tuned.step(20)
+    _, ev_r = ref.series(1, 20)
+    _, ev_t = tuned.series(1, 20)
+    assert np.array_equal(ev_r, ev_t)
+    xr, _, _, ir = ref.get_ions()
+    xt, _, _, it = tuned.get_ions()
+    assert np.array_equal(ir, it) and np.abs(xr - xt).max() < 1e-12
