@@ -180,6 +180,8 @@ def run_ours(args):
     run = od.Run(p, stream=ctypes_stream(stream))
     N = run.N
     info = run.info()
+    # pair-kernel autotuner (untimed; cached per device and ion count)
+    tv, tg, _ = od.tune_cached(run.h, "%s|N=%d" % (torch.cuda.get_device_name(local), N))
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
 
     for _ in range(args.warmup):
@@ -252,7 +254,9 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": desc, "n_ions": N, "n_dust": run.D, "steps_timed": args.steps,
                    "l2": "flushed between timed steps (256 MB write)", "parallelism": "replicas" if world > 1 else "1 GPU",
-                   "precision": "pair forces FP32; ion state, grain sums and averages FP64"},
+                   "precision": "pair forces FP32; ion state, grain sums and averages FP64",
+                   "pair_kernel": {"threads": od.force_variant_shape(tv)[0], "targets_per_thread":
+                                   od.force_variant_shape(tv)[1], "units_per_block": tg}},
         "ion_steps_per_s": world * float(N) * args.steps / (t_max / 1e3),
         "wall_s_timed": wall,
         "kernel_ms_per_step": {"push_scan_inject": kms[0] / max(kn[0], 1), "pair_forces": k1_ms,

@@ -166,6 +166,14 @@ int od_tune(od_handle* h, int reps, double* ms, int* best_variant, int* best_uni
 int od_set_force_config(od_handle* h, int variant, int units_per_block);
 int od_get_force_config(od_handle* h, int* variant, int* units_per_block, int* n_variants);
 
+/* Failure-detection self-test (no counterpart in the paper): runs one push/scan kernel in
+ * which the first scan tile withholds its prefix, so the look-back wait of the next
+ * tile finds no inclusive prefix and gives up after `polls` polls instead of its usual
+ * ~4 s limit.  Expected return: OD_ETIMEOUT, with the GPU context still usable.  The
+ * run's ion state is left inconsistent: destroy the handle afterwards.  Needs more than
+ * 256 ions. */
+int od_selftest_wait_timeout(od_handle* h, int64_t polls);
+
 /* Text of the last error on h, or of the last failed call without a handle (od_create,
  * od_pair_accel_static) when h is NULL. */
 const char* od_last_error(const od_handle* h);

@@ -101,7 +101,8 @@ def lib():
         L.od_tune.argtypes = [vp, ctypes.c_int, vp, vp, vp]
         L.od_set_force_config.argtypes = [vp, ctypes.c_int, ctypes.c_int]
         L.od_get_force_config.argtypes = [vp, vp, vp, vp]
-        for name in ("od_tune", "od_set_force_config", "od_get_force_config"):
+        L.od_selftest_wait_timeout.argtypes = [vp, i64]
+        for name in ("od_tune", "od_set_force_config", "od_get_force_config", "od_selftest_wait_timeout"):
             getattr(L, name).restype = ctypes.c_int
         for name in ("od_create", "od_step", "od_dust_state", "od_dust_terms", "od_series", "od_counters",
                      "od_dust_now", "od_set_ions", "od_info", "od_set_profiling", "od_kernel_times"):
@@ -249,6 +250,19 @@ def od_kernel_times(h):
 def od_last_error(h=None):
     m = lib().od_last_error(h)
     return m.decode() if m else ""
+
+
+def od_selftest_wait_timeout(h, polls=2000):
+    """return code of the bounded-wait self-test (OD_ETIMEOUT = -6 expected)"""
+    return lib().od_selftest_wait_timeout(h, int(polls))
+
+
+FORCE_VARIANTS = ((64, 1), (64, 2), (128, 2), (128, 4), (256, 2), (256, 4), (128, 8), (64, 8))
+
+
+def force_variant_shape(v):
+    """(threads per block, targets per thread) of pair-kernel variant v"""
+    return FORCE_VARIANTS[v]
 
 
 def od_get_force_config(h):

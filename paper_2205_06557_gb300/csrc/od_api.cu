@@ -39,6 +39,53 @@ unsigned long long prob_threshold(double p)
     return (unsigned long long)t;
 }
 
+// App. B flux integrals of the axial distribution N(u, s^2) through the bottom face up
+// to speed v >= 0, and through the top face from speed v <= 0 up to 0
+double flux_bottom_h(double v, double u, double s)
+{
+    const double z = (v - u) / s, z0 = -u / s;
+    return u * (norm_cdf(z) - norm_cdf(z0)) + s * (norm_pdf(z0) - norm_pdf(z));
+}
+
+double flux_top_h(double v, double u, double s)
+{
+    const double z = (v - u) / s, z0 = -u / s;
+    return -u * (norm_cdf(z0) - norm_cdf(z)) + s * (norm_pdf(z0) - norm_pdf(z));
+}
+
+// inverse flux CDFs at U = k / VTAB_K for both faces (bisection to FP64 resolution);
+// layout: bottom [0..K], top [K+1..2K+1]
+void build_vtab(double u, double s, std::vector<double>& tab, double& gmax_b, double& gmax_t)
+{
+    const int K = VTAB_K;
+    tab.assign(2 * (K + 1), 0.0);
+    const double vb = std::max(u, 0.0) + 12.0 * s;
+    gmax_b = flux_bottom_h(vb, u, s);
+    for (int k = 0; k <= K; ++k) {
+        const double target = (double)k / K * gmax_b;
+        double lo = k > 0 ? tab[k - 1] : 0.0, hi = vb;
+        for (int it = 0; it < 200 && hi - lo > 1e-15 * vb; ++it) {
+            const double mid = 0.5 * (lo + hi);
+            if (flux_bottom_h(mid, u, s) < target) lo = mid;
+            else hi = mid;
+        }
+        tab[k] = k == K ? vb : 0.5 * (lo + hi);
+    }
+    const double vt = std::min(u, 0.0) - 12.0 * s;
+    gmax_t = flux_top_h(vt, u, s);
+    double* tt = tab.data() + K + 1;
+    for (int k = 0; k <= K; ++k) {
+        const double target = (double)k / K * gmax_t;
+        double lo = vt, hi = k > 0 ? tt[k - 1] : 0.0;
+        for (int it = 0; it < 200 && hi - lo > 1e-15 * (-vt); ++it) {
+            const double mid = 0.5 * (lo + hi);
+            if (flux_top_h(mid, u, s) > target) lo = mid;
+            else hi = mid;
+        }
+        tt[k] = k == K ? vt : 0.5 * (lo + hi);
+    }
+}
+
 // paper's monomial order of Eq. (Polinomial): alpha_t multiplies r^(2 a_t) z^(2 b_t)
 const int kPowR[15] = {0, 1, 0, 1, 2, 0, 2, 1, 3, 0, 2, 3, 1, 4, 0};
 const int kPowZ[15] = {0, 0, 1, 1, 0, 2, 1, 2, 0, 3, 2, 1, 3, 0, 4};
@@ -148,6 +195,7 @@ struct od_handle {
     double kms[4] = {0, 0, 0, 0};
     long long klaunch[4] = {0, 0, 0, 0};
     double* d_stats = nullptr;
+    double* d_vtab = nullptr;
     double* d_series = nullptr;
     int* d_evseries = nullptr;
 };
@@ -301,6 +349,8 @@ void derive(const od_params* p, Phys& P, od_handle* h)
     P.avg_start = p->avg_start > 0 ? p->avg_start : 1;
     P.Ie0 = Z * p->n_inf * std::sqrt(8.0 * kKB * p->T_e / (kPI * kME)) / 4.0;
     P.e_over_kTe = kQE / (kKB * p->T_e);
+    P.spin_limit = SPIN_LIMIT;
+    P.test_hold_tile0 = 0;
     const long long N = p->n_ions > 0 ? p->n_ions : std::llround(p->n_inf * kPI * p->R * p->R * p->H / p->weight);
     P.N = (int)N;
     double* o = h->info;
@@ -505,6 +555,7 @@ void free_all(od_handle* h)
     cudaFree(h->B.dpart);
     cudaFree(h->B.ctrl);
     cudaFree(h->d_stats);
+    cudaFree(h->d_vtab);
     cudaFree(h->d_series);
     cudaFree(h->d_evseries);
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
@@ -526,6 +577,14 @@ int create_impl(const od_params* p, od_handle* h)
         h->own_stream = true;
     }
     derive(p, h->P, h);
+    {
+        std::vector<double> tab;
+        build_vtab(h->P.u, h->P.sig, tab, h->P.gmax_b, h->P.gmax_t);
+        OD_CK(h, cudaMalloc(&h->d_vtab, sizeof(double) * tab.size()));
+        OD_CK(h, cudaMemcpyAsync(h->d_vtab, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice, h->stream));
+        OD_CK(h, cudaStreamSynchronize(h->stream));
+        h->P.vtab = h->d_vtab;
+    }
     const bool eout_on = !(p->flags & OD_F_NO_EOUT);
     if (p->eout_coeffs) {
         std::memcpy(h->alpha, p->eout_coeffs, sizeof(double) * 15);
@@ -912,6 +971,19 @@ int od_tune(od_handle* h, int reps, double* ms, int* best_variant, int* best_upb
     OD_CK(h, cudaStreamSynchronize(h->stream));
     if (best_variant) *best_variant = bv;
     if (best_upb) *best_upb = bg;
+    return read_error_word(h);
+}
+
+int od_selftest_wait_timeout(od_handle* h, int64_t polls)
+{
+    if (!h || polls < 1) return fail(h, OD_EINVAL, "bad handle or poll limit");
+    if (h->P.N <= push_tile()) return fail(h, OD_EINVAL, "the wait self-test needs more than one scan tile");
+    Phys P = h->P;
+    P.spin_limit = polls;
+    P.test_hold_tile0 = 1;
+    OD_LK(h, launch_push_scan(P, h->B, h->stream));
+    OD_CK(h, cudaStreamSynchronize(h->stream));
+    h->graph_ok = false;
     return read_error_word(h);
 }
 

@@ -19,6 +19,8 @@ constexpr int ERR_NAN = 1;
 constexpr int ERR_TIMEOUT = 2;
 constexpr int ERR_OVERFLOW = 4;
 constexpr int ERR_PLACE = 8;
+constexpr long long SPIN_LIMIT = 1ll << 22;  // ~4 s of polling with the 1 us back-off
+constexpr int VTAB_K = 4096;                  // intervals of the tabulated inverse flux CDFs
 
 // Philox streams (fourth counter word): the same layout on host and device.
 enum : uint32_t { ST_INIT_POS = 0, ST_INIT_VEL = 1, ST_COLL = 2, ST_COLL_VEL = 3, ST_INJ_A = 4, ST_INJ_B = 5 };
@@ -82,6 +84,12 @@ struct Phys {
     double Ie0;      // OML electron flux at zero potential per unit area, 1/(m^2 s)
     double e_over_kTe;
     double inv4pieps0;
+    // App. B inverse flux CDFs tabulated at U = k / VTAB_K (bottom face, then top face):
+    // starting points and brackets for the Newton polish of every injected axial speed
+    const double* vtab;
+    double gmax_b, gmax_t;  // flux integrals G(v_max) and G_top(v_min) the CDFs are normalised by
+    long long spin_limit;  // polls before a device-side wait gives up (ERR_TIMEOUT)
+    int test_hold_tile0;   // wait self-test: the first scan tile never publishes its prefix
 };
 
 // Device buffers. Ion state is double-buffered (compaction writes the other copy).

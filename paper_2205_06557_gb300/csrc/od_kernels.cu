@@ -97,10 +97,9 @@ __device__ double flux_top(double v, double u, double s)
 // F(v) - target with derivative |v| N(v; u, s^2), kept inside a shrinking bracket
 // (bisection when a step leaves it).
 template <bool TOP>
-__device__ double invert_flux(double target, double lo, double hi, double u, double s)
+__device__ double invert_flux(double target, double lo, double hi, double v, double u, double s)
 {
-    double v = 0.5 * (lo + hi);
-    for (int it = 0; it < 200; ++it) {
+    for (int it = 0; it < 100; ++it) {
         const double F = TOP ? flux_top(v, u, s) : flux_bottom(v, u, s);
         const double g = TOP ? (target - F) : (F - target);  // increasing in v
         if (g < 0) lo = v;
@@ -108,9 +107,11 @@ __device__ double invert_flux(double target, double lo, double hi, double u, dou
         const double dg = fabs(v) * npdf((v - u) / s) / s;
         double vn = dg > 0 ? v - g / dg : 0.5 * (lo + hi);
         if (!(vn > lo && vn < hi)) vn = 0.5 * (lo + hi);
-        const double step = fabs(vn - v);
+        // converged to ~1e-13 of the speed scale (a few hundred ulp above FP64 rounding)
+        const double tol = 1e-13 * fmax(fabs(vn), s);
+        const bool done = fabs(vn - v) <= tol || hi - lo <= tol;
         v = vn;
-        if (step <= 1e-15 * s || hi - lo <= 1e-15 * s) break;
+        if (done) break;
     }
     return v;
 }
@@ -132,14 +133,20 @@ __device__ void sample_injection(const Phys& P, unsigned long long id, uint32_t 
         o.z = f == 0 ? -0.5 * P.H : 0.5 * P.H;
         o.vx = P.sig * n0;
         o.vy = P.sig * n1;
+        // flux-weighted axial speed: the tabulated inverse CDF brackets the root and gives
+        // the starting point, Newton polishes it to ~1e-13 (FP64 is slow on this GPU: a
+        // few iterations instead of a bisection from the whole range)
         const double U = unif(A.w);
-        if (f == 0) {
-            const double hi = fmax(P.u, 0.0) + 12.0 * P.sig;
-            o.vz = invert_flux<false>(U * flux_bottom(hi, P.u, P.sig), 0.0, hi, P.u, P.sig);
-        } else {
-            const double lo = fmin(P.u, 0.0) - 12.0 * P.sig;
-            o.vz = invert_flux<true>(U * flux_top(lo, P.u, P.sig), lo, 0.0, P.u, P.sig);
-        }
+        const double xk = U * VTAB_K;
+        const int k = min((int)xk, VTAB_K - 1);
+        const double* tab = P.vtab + (f == 0 ? 0 : VTAB_K + 1);
+        const double t0 = tab[k], t1 = tab[k + 1];
+        const double pad = 1e-12 * fmax(fmax(fabs(t0), fabs(t1)), P.sig);
+        const double v0 = t0 + (xk - k) * (t1 - t0);
+        if (f == 0)
+            o.vz = invert_flux<false>(U * P.gmax_b, fmax(fmin(t0, t1) - pad, 0.0), fmax(t0, t1) + pad, v0, P.u, P.sig);
+        else
+            o.vz = invert_flux<true>(U * P.gmax_t, fmin(t0, t1) - pad, fmin(fmax(t0, t1) + pad, 0.0), v0, P.u, P.sig);
         o.face = f;
     } else {
         double s, c;
@@ -244,7 +251,7 @@ __global__ void k_fpos(Phys P, Bufs B, int buf, double ls_inv)
 
 // ------------------------------------------------- push + scan + compaction
 constexpr int PUSH_BT = 256;
-constexpr long long SPIN_LIMIT = 1ll << 22;
+
 constexpr unsigned FLAG_A = 1u, FLAG_P = 2u;
 
 __device__ __forceinline__ unsigned long long pack_status(uint32_t epoch, unsigned flag, int val)
@@ -340,41 +347,57 @@ __global__ void __launch_bounds__(BT) k_push_scan(Phys P, Bufs B, int n_tiles, d
 
     // decoupled look-back across tiles (tile ids are taken in launch order, so every
     // predecessor is running or done); the wait is bounded and reports ERR_TIMEOUT
-    if (threadIdx.x == 0) {
+    // warp 0 probes 32 predecessors per read: lane l looks at tile base - l
+    if (warp == 0) {
         const int total = s_total;
         unsigned long long* st = B.tile_status;
         int excl = 0;
         if (tile == 0) {
-            st_release_u64(st, pack_status(sn, FLAG_P, total));
+            // (the wait self-test withholds tile 0's prefix so that its successors time out)
+            if (lane == 0 && !P.test_hold_tile0) st_release_u64(st, pack_status(sn, FLAG_P, total));
         } else {
-            st_release_u64(st + tile, pack_status(sn, FLAG_A, total));
-            int t = tile - 1;
+            if (lane == 0) st_release_u64(st + tile, pack_status(sn, FLAG_A, total));
+            int base = tile - 1;
             long long spins = 0;
             unsigned ns = 32;
-            while (t >= 0) {
-                const unsigned long long w = ld_acquire_u64(st + t);
-                const uint32_t ep = (uint32_t)(w >> 32);
-                const unsigned fl = (unsigned)(w >> 30) & 3u;
-                if (ep != sn || fl == 0u) {
-                    if (++spins > SPIN_LIMIT) {
-                        atomicOr(&C->err, ERR_TIMEOUT);
+            while (true) {
+                const int t = base - lane;
+                unsigned fl = FLAG_P;  // before tile 0: an inclusive prefix of zero
+                int val = 0;
+                if (t >= 0) {
+                    const unsigned long long w = ld_acquire_u64(st + t);
+                    fl = (uint32_t)(w >> 32) == sn ? (unsigned)(w >> 30) & 3u : 0u;
+                    val = (int)(w & 0x3fffffffull);
+                }
+                const unsigned pmask = __ballot_sync(0xffffffffu, fl == FLAG_P);
+                const unsigned zmask = __ballot_sync(0xffffffffu, fl == 0u);
+                const int first_p = pmask ? __ffs(pmask) - 1 : 32;  // nearest inclusive prefix
+                const unsigned need = first_p >= 31 ? 0xffffffffu : ((1u << (first_p + 1)) - 1u);
+                if (zmask & need) {  // a tile up to that prefix has not published yet
+                    if (++spins > P.spin_limit) {
+                        if (lane == 0) atomicOr(&C->err, ERR_TIMEOUT);
                         break;
                     }
                     __nanosleep(ns);
                     if (ns < 1024) ns *= 2;
                     continue;
                 }
-                excl += (int)(w & 0x3fffffffull);
-                if (fl == FLAG_P) break;
-                --t;
+                int contrib = lane <= first_p ? val : 0;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) contrib += __shfl_down_sync(0xffffffffu, contrib, o);
+                excl += __shfl_sync(0xffffffffu, contrib, 0);
+                if (first_p < 32) break;
+                base -= 32;
             }
-            st_release_u64(st + tile, pack_status(sn, FLAG_P, excl + total));
+            if (lane == 0) st_release_u64(st + tile, pack_status(sn, FLAG_P, excl + total));
         }
-        // keep destinations in bounds even if a wait gave up
-        if (excl > tile * BT) excl = tile * BT;
-        if (excl < 0) excl = 0;
-        s_prefix = excl;
-        atomicAdd(&C->removed_total, total);
+        if (lane == 0) {
+            // keep destinations in bounds even if a wait gave up
+            if (excl > tile * BT) excl = tile * BT;
+            if (excl < 0) excl = 0;
+            s_prefix = excl;
+            atomicAdd(&C->removed_total, total);
+        }
     }
     __syncthreads();
     const int prefix = s_prefix;
@@ -527,7 +550,7 @@ __global__ void __launch_bounds__(BT) k_forces(const float4* __restrict__ fpos, 
 }
 
 // ---------------------------------------------- kick, collisions, grain sums
-constexpr int KICK_BT = 256;
+constexpr int KICK_BT = 64;  // small blocks spread small runs over many SMs (FP64 is slow)
 
 __device__ __forceinline__ double warp_sum(double v)
 {
@@ -562,8 +585,9 @@ __global__ void __launch_bounds__(BT) k_kick(Phys P, Bufs B, ForceArgs F, int mo
             const int t = i / F.TI;
             const long long u0 = (long long)t * F.JS;
             const int g0 = owner_of(u0, F.U, F.G), g1 = owner_of(u0 + F.JS - 1, F.U, F.G);
+#pragma unroll 8
             for (int s = 0; s <= g1 - g0; ++s) {
-                const float4 p = B.part[(long long)s * F.n_pad + i];
+                const float4 p = __ldcs(B.part + (long long)s * F.n_pad + i);
                 ax += p.x;
                 ay += p.y;
                 az += p.z;
@@ -572,16 +596,19 @@ __global__ void __launch_bounds__(BT) k_kick(Phys P, Bufs B, ForceArgs F, int mo
             ay *= -P.k_ii;
             az *= -P.k_ii;
         }
-        // bare Coulomb force of the grains (asymmetric model), E_out and the driving field
-        double bx = 0.0, by = 0.0, bz = P.qm * P.E;
+        // bare Coulomb force of the grains (asymmetric model): FP32 terms from FP64
+        // separations, like the pair forces
         for (int k = 0; k < P.D; ++k) {
-            const double dx = x - P.gx[k], dy = y - P.gy[k], dz = z - P.gz[k];
-            const double r2 = dx * dx + dy * dy + dz * dz;
-            const double c = P.kdi * C->Q[k] / (r2 * sqrt(r2));
-            bx += c * dx;
-            by += c * dy;
-            bz += c * dz;
+            const float dx = (float)(x - P.gx[k]), dy = (float)(y - P.gy[k]), dz = (float)(z - P.gz[k]);
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const float ri = rsqrt_approx(r2);
+            const float c = (float)(P.kdi * C->Q[k]) * (ri * ri * ri);
+            ax = fmaf(c, dx, ax);
+            ay = fmaf(c, dy, ay);
+            az = fmaf(c, dz, az);
         }
+        // E_out (FP64 polynomial) and the driving field
+        double bx = 0.0, by = 0.0, bz = P.qm * P.E;
         if (P.eout) {
             double ex, ey, ez;
             eout_field(P, x, y, z, ex, ey, ez);
@@ -621,17 +648,21 @@ __global__ void __launch_bounds__(BT) k_kick(Phys P, Bufs B, ForceArgs F, int mo
     if (lane == 0 && bc) atomicAdd(&C->ev_step[12], __popc(bc));
 
     // grain side of Eq. 1 without the prefactor q Q_k / (4 pi eps0):
-    // sum_i (1 + rho/lambda) exp(-rho/lambda) (r_k - r_i) / rho^3, fixed-order block sums
+    // sum_i (1 + rho/lambda) exp(-rho/lambda) (r_k - r_i) / rho^3; FP32 terms from FP64
+    // separations, FP64 sums in a fixed order (warp tree, then block tree)
+    const float lam_inv = (float)P.lam_inv;
+    const float lam_inv_l2 = (float)(P.lam_inv * 1.4426950408889634);
     for (int k = 0; k < P.D; ++k) {
         double fx = 0.0, fy = 0.0, fz = 0.0;
         if (live) {
-            const double dx = P.gx[k] - x, dy = P.gy[k] - y, dz = P.gz[k] - z;
-            const double r2 = dx * dx + dy * dy + dz * dz;
-            const double rho = sqrt(r2);
-            const double f = (1.0 + rho * P.lam_inv) * exp(-rho * P.lam_inv) / (r2 * rho);
-            fx = f * dx;
-            fy = f * dy;
-            fz = f * dz;
+            const float dx = (float)(P.gx[k] - x), dy = (float)(P.gy[k] - y), dz = (float)(P.gz[k] - z);
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const float ri = rsqrt_approx(r2);
+            const float rho = r2 * ri;
+            const float f = fmaf(rho, lam_inv, 1.0f) * ex2_approx(-rho * lam_inv_l2) * (ri * ri * ri);
+            fx = (double)(f * dx);
+            fy = (double)(f * dy);
+            fz = (double)(f * dz);
         }
         fx = warp_sum(fx);
         fy = warp_sum(fy);
@@ -744,15 +775,18 @@ __global__ void __launch_bounds__(DUST_BT) k_dust(Phys P, Bufs B, int nb, int mo
             for (int j = 0; j < REC; ++j) C->wsum[k][j] += s_rec[k][j];
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        if (step < C->series_cap)
-            for (int j = 0; j < EV; ++j) C->evseries[step * EV + j] = C->ev_step[j];
-        for (int j = 0; j < 13; ++j) C->counters[j] += C->ev_step[j];
+    // one thread per event counter: record, accumulate, reset for the next step
+    const int j = threadIdx.x;
+    if (j < EV) {
+        const int e = C->ev_step[j];
+        if (step < C->series_cap) C->evseries[step * EV + j] = e;
+        C->counters[j] += e;
+        C->ev_step[j] = 0;
+    } else if (j == 32) {
         C->counters[13] = sn;
         C->counters[14] = P.N;
         C->counters[15] = (long long)C->next_id;
         if (sn >= P.avg_start) C->wcount += 1;
-        for (int j = 0; j < EV; ++j) C->ev_step[j] = 0;
         C->removed_total = 0;
         C->step = sn;
     }
