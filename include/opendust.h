@@ -166,6 +166,32 @@ int od_tune(od_handle* h, int reps, double* ms, int* best_variant, int* best_uni
 int od_set_force_config(od_handle* h, int variant, int units_per_block);
 int od_get_force_config(od_handle* h, int* variant, int* units_per_block, int* n_variants);
 
+/* ---- batches: many independent runs in one launch per step ----
+ * The paper's sweeps (Sec. 4: drag versus Mach number, versus collision frequency)
+ * are sets of independent runs.  A batch advances R runs of uneven ion count with ONE
+ * persistent kernel launch per step (replayed from a CUDA graph): the runs' step phases
+ * are tasks taken by a resident grid in dependency order.
+ *   od_create_batch   ps[R] (host, copied; ps[0].cuda_stream is used for the batch, the
+ *                     other streams are ignored); each run is created as by od_create
+ *   od_batch_step     n steps of every run; same error codes as od_step (first failing run)
+ *   od_batch_run      the handle of run r, for every read call (od_dust_state, od_series,
+ *                     od_counters, od_get_ions, od_info ...); the batch owns it: do not
+ *                     destroy it, step it, replace its ions or tune it on its own
+ *   od_batch_tune     times the pair tasks at targets-per-thread {1,2,4} x source-chunk
+ *                     {2048,4096,8192} (ms[9], host, may be NULL), keeps the fastest; the
+ *                     runs' states are not changed
+ *   od_batch_set_config applies a known choice; od_destroy_batch frees everything
+ *   od_batch_last_error text of the last error on b (or of the last failed create). */
+typedef struct od_batch od_batch;
+int od_create_batch(const od_params* ps, int32_t R, od_batch** out);
+int od_batch_step(od_batch* b, int64_t n);
+od_handle* od_batch_run(od_batch* b, int32_t r);
+int od_batch_size(const od_batch* b);
+int od_batch_tune(od_batch* b, int reps, double* ms, int* best_targets_per_thread, int* best_chunk);
+int od_batch_set_config(od_batch* b, int targets_per_thread, int chunk);
+void od_destroy_batch(od_batch* b);
+const char* od_batch_last_error(const od_batch* b);
+
 /* Failure-detection self-test (no counterpart in the paper): runs one push/scan kernel in
  * which the first scan tile withholds its prefix, so the look-back wait of the next
  * tile finds no inclusive prefix and gives up after `polls` polls instead of its usual

@@ -102,6 +102,19 @@ def lib():
         L.od_set_force_config.argtypes = [vp, ctypes.c_int, ctypes.c_int]
         L.od_get_force_config.argtypes = [vp, vp, vp, vp]
         L.od_selftest_wait_timeout.argtypes = [vp, i64]
+        L.od_create_batch.argtypes = [vp, i32, P(vp)]
+        L.od_batch_step.argtypes = [vp, i64]
+        L.od_batch_run.argtypes = [vp, i32]
+        L.od_batch_run.restype = vp
+        L.od_batch_size.argtypes = [vp]
+        L.od_batch_tune.argtypes = [vp, ctypes.c_int, vp, vp, vp]
+        L.od_batch_set_config.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+        L.od_destroy_batch.argtypes = [vp]
+        L.od_destroy_batch.restype = None
+        L.od_batch_last_error.argtypes = [vp]
+        L.od_batch_last_error.restype = ctypes.c_char_p
+        for name in ("od_create_batch", "od_batch_step", "od_batch_size", "od_batch_tune", "od_batch_set_config"):
+            getattr(L, name).restype = ctypes.c_int
         for name in ("od_tune", "od_set_force_config", "od_get_force_config", "od_selftest_wait_timeout"):
             getattr(L, name).restype = ctypes.c_int
         for name in ("od_create", "od_step", "od_dust_state", "od_dust_terms", "od_series", "od_counters",
@@ -325,21 +338,69 @@ def od_pair_accel_static(x_dev, n, lambda_De, k, a_dev, stream=None):
                                              ctypes.c_void_p(a_dev), ctypes.c_void_p(stream) if stream else None))
 
 
+def _bcheck(rc, b=None):
+    if rc < 0:
+        msg = lib().od_batch_last_error(b)
+        raise OdError(int(rc), msg.decode() if msg else "")
+    return rc
+
+
+def od_create_batch(plist, stream=None):
+    built = [make_params(p, stream if k == 0 else None) for k, p in enumerate(plist)]
+    arr = (od_params * len(built))(*[s for s, _ in built])
+    b = ctypes.c_void_p()
+    _bcheck(lib().od_create_batch(arr, len(built), ctypes.byref(b)))
+    return b
+
+
+def od_batch_step(b, n):
+    return _bcheck(lib().od_batch_step(b, int(n)), b)
+
+
+def od_batch_run(b, r):
+    return ctypes.c_void_p(lib().od_batch_run(b, int(r)))
+
+
+def od_batch_tune(b, reps=2):
+    ms = np.zeros(9)
+    bi, bj = ctypes.c_int(), ctypes.c_int()
+    _bcheck(lib().od_batch_tune(b, int(reps), _ptr(ms), ctypes.byref(bi), ctypes.byref(bj)), b)
+    return ms.reshape(3, 3), bi.value, bj.value
+
+
+def od_batch_set_config(b, targets_per_thread, chunk):
+    return _bcheck(lib().od_batch_set_config(b, int(targets_per_thread), int(chunk)), b)
+
+
+def od_destroy_batch(b):
+    if b is not None:
+        lib().od_destroy_batch(b)
+
+
 class Run:
-    """Convenience owner of one handle (create on construction, destroy on close)."""
+    """Convenience owner of one handle (create on construction, destroy on close).
+    Run.view(handle, n_dust) wraps a batch member without owning it."""
 
     def __init__(self, p, stream=None):
         self.D = len(p.get("dust", [])) if isinstance(p, dict) else p.n_dust
         self.h = od_create(p, stream)
+        self.owned = True
         self.N = int(od_info(self.h)["N"])
+
+    @classmethod
+    def view(cls, h, n_dust):
+        r = cls.__new__(cls)
+        r.D, r.h, r.owned = n_dust, h, False
+        r.N = int(od_info(h)["N"])
+        return r
 
     def step(self, n=1):
         od_step(self.h, n)
 
     def close(self):
-        if self.h is not None:
+        if self.h is not None and self.owned:
             od_destroy(self.h)
-            self.h = None
+        self.h = None
 
     def __del__(self):
         try:
@@ -370,3 +431,30 @@ class Run:
 
     def set_ions(self, x, v, ids, next_id, a=None):
         od_set_ions(self.h, x, v, ids, next_id, a)
+
+
+class Batch:
+    """Owner of a batch of independent runs stepped by one launch per step."""
+
+    def __init__(self, plist, stream=None):
+        self.b = od_create_batch(plist, stream)
+        self.runs = [Run.view(od_batch_run(self.b, r), len(p.get("dust", []))) for r, p in enumerate(plist)]
+
+    def step(self, n=1):
+        od_batch_step(self.b, n)
+
+    def tune(self, reps=2):
+        return od_batch_tune(self.b, reps)
+
+    def close(self):
+        if self.b is not None:
+            for r in self.runs:
+                r.h = None
+            od_destroy_batch(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

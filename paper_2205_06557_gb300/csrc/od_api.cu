@@ -175,6 +175,7 @@ struct od_handle {
     ForceArgs F{};
     int variant = 0;
     int upb = 8;  // pair-kernel work units per persistent block
+    bool batch_member = false;  // stepped only through its batch (od_batch_step)
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     cudaGraph_t graph = nullptr;
@@ -660,6 +661,7 @@ int od_create(const od_params* p, od_handle** out)
 int od_step(od_handle* h, int64_t n)
 {
     if (!h || n < 0) return fail(h, OD_EINVAL, "bad handle or step count");
+    if (h->batch_member) return fail(h, OD_EINVAL, "this run belongs to a batch: step it with od_batch_step");
     if (n == 0) return OD_OK;
     int rc = ensure_series(h, h->host_step + n);
     if (rc) return rc;
@@ -835,6 +837,7 @@ int od_set_ions(od_handle* h, const double* x, const double* v, const double* a,
                 uint64_t next_id)
 {
     if (!h || n < 0 || (n > 0 && (!x || !v || !id))) return fail(h, OD_EINVAL, "bad argument");
+    if (h->batch_member) return fail(h, OD_EINVAL, "the ions of a batch member cannot be replaced");
     if (n > h->cap) return fail(h, OD_EOVERFLOW, "more ions than the handle's capacity");
     const int buf = (int)(h->host_step & 1);
     std::vector<double> tmp(3 * (size_t)n);
@@ -923,8 +926,9 @@ static int apply_force_config(od_handle* h, int variant, int upb)
 
 int od_set_force_config(od_handle* h, int variant, int units_per_block)
 {
-    if (!h || variant < 0 || variant >= num_force_variants() || units_per_block < 1 || units_per_block > 1024)
-        return fail(h, OD_EINVAL, "bad force configuration");
+    if (!h || variant < 0 || variant >= num_force_variants() || units_per_block < 1 || units_per_block > 1024 ||
+        h->batch_member)
+        return fail(h, OD_EINVAL, "bad force configuration (or a batch member: use od_batch_set_config)");
     int rc = apply_force_config(h, variant, units_per_block);
     if (rc) return rc;
     OD_CK(h, cudaStreamSynchronize(h->stream));
@@ -933,7 +937,8 @@ int od_set_force_config(od_handle* h, int variant, int units_per_block)
 
 int od_tune(od_handle* h, int reps, double* ms, int* best_variant, int* best_upb)
 {
-    if (!h || reps < 1) return fail(h, OD_EINVAL, "bad handle or repetition count");
+    if (!h || reps < 1 || h->batch_member)
+        return fail(h, OD_EINVAL, "bad handle or repetition count (or a batch member: use od_batch_tune)");
     const int nv = num_force_variants();
     if (ms)
         for (int i = 0; i < nv * 4; ++i) ms[i] = -1.0;
@@ -995,5 +1000,295 @@ int od_get_force_config(od_handle* h, int* variant, int* units_per_block, int* n
     if (n_variants) *n_variants = num_force_variants();
     return OD_OK;
 }
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ batches
+struct od_batch {
+    std::vector<od_handle*> runs;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    RunDesc* d_runs = nullptr;
+    int2* d_tasks = nullptr;
+    int2* d_tasks_f = nullptr;  // pair units only (tuning)
+    unsigned long long* d_done = nullptr;
+    BatchCtrl* d_bc = nullptr;
+    BatchCtrl* d_bc_f = nullptr;
+    long long T = 0, T_f = 0;
+    int4 phase_end{0, 0, 0, 0};
+    int ipt = 2, jc = 4096, grid = 1, sms = 1;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    bool graph_ok = false;
+    long long host_step = 0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_batch_error;
+
+int bfail(od_batch* b, int code, const std::string& msg)
+{
+    if (b) b->err = msg;
+    else g_batch_error = msg;
+    return code;
+}
+
+#define OD_BCK(b, call)                                                                              \
+    do {                                                                                             \
+        cudaError_t e_ = (call);                                                                     \
+        if (e_ != cudaSuccess)                                                                       \
+            return bfail(b, e_ == cudaErrorMemoryAllocation ? OD_ENOMEM : OD_ECUDA,                  \
+                         std::string(#call) + ": " + cudaGetErrorString(e_));                        \
+    } while (0)
+
+// apply the batch pair plan (ipt, jc) to every run and rebuild the task lists
+int batch_build(od_batch* b)
+{
+    const int R = (int)b->runs.size();
+    std::vector<RunDesc> desc(R);
+    std::vector<int2> tA, tF, tK, tD;
+    for (int r = 0; r < R; ++r) {
+        od_handle* h = b->runs[r];
+        h->F = batch_plan(h->P.N, b->ipt, b->jc);
+        h->P.n_pad = h->F.n_pad;
+        if (h->F.n_pad > h->npad_cap) return bfail(b, OD_EOVERFLOW, "padded ion count exceeds a run's buffer");
+        int rc = ensure_part(h);
+        if (rc) return bfail(b, rc, h->err);
+        rc = launch_fpos(h->P, h->B, (int)(h->host_step & 1), b->stream);
+        if (rc) return bfail(b, OD_ECUDA, "batch: position refresh failed");
+        desc[r].P = h->P;
+        desc[r].B = h->B;
+        desc[r].F = h->F;
+        desc[r].nA = (h->P.N + BATCH_TILE - 1) / BATCH_TILE;
+        desc[r].nK = desc[r].nA;
+        for (int i = 0; i < desc[r].nA; ++i) tA.push_back(make_int2(r, i));
+        for (long long u = 0; u < h->F.U; ++u) tF.push_back(make_int2(r, (int)u));
+        for (int i = 0; i < desc[r].nK; ++i) tK.push_back(make_int2(r, i));
+        tD.push_back(make_int2(r, 0));
+    }
+    std::vector<int2> all;
+    all.insert(all.end(), tA.begin(), tA.end());
+    all.insert(all.end(), tF.begin(), tF.end());
+    all.insert(all.end(), tK.begin(), tK.end());
+    all.insert(all.end(), tD.begin(), tD.end());
+    b->phase_end = make_int4((int)tA.size(), (int)(tA.size() + tF.size()), (int)(tA.size() + tF.size() + tK.size()),
+                             (int)all.size());
+    b->T = (long long)all.size();
+    b->T_f = (long long)tF.size();
+    cudaFree(b->d_runs);
+    cudaFree(b->d_tasks);
+    cudaFree(b->d_tasks_f);
+    b->d_runs = nullptr;
+    b->d_tasks = b->d_tasks_f = nullptr;
+    OD_BCK(b, cudaMalloc(&b->d_runs, sizeof(RunDesc) * R));
+    OD_BCK(b, cudaMalloc(&b->d_tasks, sizeof(int2) * std::max<size_t>(all.size(), 1)));
+    OD_BCK(b, cudaMalloc(&b->d_tasks_f, sizeof(int2) * std::max<size_t>(tF.size(), 1)));
+    OD_BCK(b, cudaMemcpyAsync(b->d_runs, desc.data(), sizeof(RunDesc) * R, cudaMemcpyHostToDevice, b->stream));
+    OD_BCK(b, cudaMemcpyAsync(b->d_tasks, all.data(), sizeof(int2) * all.size(), cudaMemcpyHostToDevice, b->stream));
+    if (!tF.empty())
+        OD_BCK(b, cudaMemcpyAsync(b->d_tasks_f, tF.data(), sizeof(int2) * tF.size(), cudaMemcpyHostToDevice, b->stream));
+    b->grid = (int)std::max(1ll, std::min<long long>((long long)batch_blocks_per_sm(b->ipt) * b->sms, b->T));
+    OD_BCK(b, cudaStreamSynchronize(b->stream));
+    b->graph_ok = false;
+    return OD_OK;
+}
+
+void batch_free(od_batch* b)
+{
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    for (od_handle* h : b->runs) {
+        free_all(h);
+        delete h;
+    }
+    cudaFree(b->d_runs);
+    cudaFree(b->d_tasks);
+    cudaFree(b->d_tasks_f);
+    cudaFree(b->d_done);
+    cudaFree(b->d_bc);
+    cudaFree(b->d_bc_f);
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->e0) cudaEventDestroy(b->e0);
+    if (b->e1) cudaEventDestroy(b->e1);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+}
+
+int batch_check(od_batch* b)
+{
+    BatchCtrl bc;
+    OD_BCK(b, cudaMemcpyAsync(&bc, b->d_bc, sizeof(bc), cudaMemcpyDeviceToHost, b->stream));
+    OD_BCK(b, cudaStreamSynchronize(b->stream));
+    if (bc.err & ERR_TIMEOUT) return bfail(b, OD_ETIMEOUT, "batch: a task's dependency wait hit its limit");
+    for (size_t r = 0; r < b->runs.size(); ++r) {
+        const int rc = read_error_word(b->runs[r]);
+        if (rc) return bfail(b, rc, "run " + std::to_string(r) + ": " + b->runs[r]->err);
+    }
+    return OD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int od_create_batch(const od_params* ps, int32_t R, od_batch** out)
+{
+    if (!out || !ps || R < 1) return bfail(nullptr, OD_EINVAL, "bad batch arguments");
+    *out = nullptr;
+    for (int r = 0; r < R; ++r) {
+        std::string msg;
+        const int rc = validate(ps + r, msg);
+        if (rc) return bfail(nullptr, rc, "run " + std::to_string(r) + ": " + msg);
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return bfail(nullptr, OD_ENODEV, "no CUDA device");
+    od_batch* b = new od_batch();
+    int rc = OD_OK;
+    auto fail_out = [&](int code) {
+        g_batch_error = b->err;
+        batch_free(b);
+        delete b;
+        return code;
+    };
+    if (ps[0].cuda_stream) {
+        b->stream = (cudaStream_t)ps[0].cuda_stream;
+    } else if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        b->err = "stream creation failed";
+        return fail_out(OD_ECUDA);
+    } else {
+        b->own_stream = true;
+    }
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+    for (int r = 0; r < R; ++r) {
+        od_params p = ps[r];
+        p.cuda_stream = b->stream;
+        od_handle* h = new od_handle();
+        rc = create_impl(&p, h);
+        if (rc) {
+            b->err = "run " + std::to_string(r) + ": " + h->err;
+            free_all(h);
+            delete h;
+            return fail_out(rc);
+        }
+        h->batch_member = true;
+        h->own_stream = false;
+        b->runs.push_back(h);
+    }
+    if (cudaMalloc(&b->d_done, sizeof(unsigned long long) * 3 * R) != cudaSuccess ||
+        cudaMalloc(&b->d_bc, sizeof(BatchCtrl)) != cudaSuccess || cudaMalloc(&b->d_bc_f, sizeof(BatchCtrl)) != cudaSuccess ||
+        cudaEventCreate(&b->e0) != cudaSuccess || cudaEventCreate(&b->e1) != cudaSuccess) {
+        b->err = "batch allocation failed";
+        return fail_out(OD_ENOMEM);
+    }
+    cudaMemsetAsync(b->d_done, 0, sizeof(unsigned long long) * 3 * R, b->stream);
+    cudaMemsetAsync(b->d_bc, 0, sizeof(BatchCtrl), b->stream);
+    rc = batch_build(b);
+    if (rc) return fail_out(rc);
+    *out = b;
+    return OD_OK;
+}
+
+int od_batch_step(od_batch* b, int64_t n)
+{
+    if (!b || n < 0) return bfail(b, OD_EINVAL, "bad batch or step count");
+    if (n == 0) return OD_OK;
+    for (od_handle* h : b->runs) {
+        const int rc = ensure_series(h, h->host_step + n);
+        if (rc) return bfail(b, rc, h->err);
+    }
+    if (!b->graph_ok) {
+        if (b->gexec) cudaGraphExecDestroy(b->gexec);
+        if (b->graph) cudaGraphDestroy(b->graph);
+        b->gexec = nullptr;
+        b->graph = nullptr;
+        OD_BCK(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+        const int lrc = launch_batch(b->ipt, b->grid, b->d_runs, b->d_tasks, b->phase_end, b->T, b->d_bc, b->d_done,
+                                     (int)b->runs.size(), SPIN_LIMIT, 0, b->stream);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+        if (lrc) return bfail(b, OD_ECUDA, std::string("batch launch: ") + cudaGetErrorString((cudaError_t)lrc));
+        if (e != cudaSuccess) return bfail(b, OD_ECUDA, std::string("batch capture: ") + cudaGetErrorString(e));
+        b->graph = g;
+        OD_BCK(b, cudaGraphInstantiate(&b->gexec, g, 0));
+        b->graph_ok = true;
+    }
+    for (int64_t s = 0; s < n; ++s) OD_BCK(b, cudaGraphLaunch(b->gexec, b->stream));
+    for (od_handle* h : b->runs) h->host_step += n;
+    b->host_step += n;
+    return batch_check(b);
+}
+
+od_handle* od_batch_run(od_batch* b, int32_t r)
+{
+    if (!b || r < 0 || r >= (int)b->runs.size()) return nullptr;
+    return b->runs[r];
+}
+
+int od_batch_size(const od_batch* b) { return b ? (int)b->runs.size() : 0; }
+
+int od_batch_tune(od_batch* b, int reps, double* ms, int* best_ipt, int* best_jc)
+{
+    if (!b || reps < 1) return bfail(b, OD_EINVAL, "bad batch or repetition count");
+    static const int ipts[3] = {1, 2, 4};
+    static const int jcs[3] = {2048, 4096, 8192};
+    double best = 1e300;
+    int bi = b->ipt, bj = b->jc;
+    for (int a = 0; a < 3; ++a)
+        for (int c = 0; c < 3; ++c) {
+            b->ipt = ipts[a];
+            b->jc = jcs[c];
+            int rc = batch_build(b);
+            if (rc) return rc;
+            OD_BCK(b, cudaMemsetAsync(b->d_bc_f, 0, sizeof(BatchCtrl), b->stream));
+            const int grid = (int)std::max(1ll, std::min<long long>((long long)batch_blocks_per_sm(b->ipt) * b->sms, b->T_f));
+            const int R = (int)b->runs.size();
+            int lrc = launch_batch(b->ipt, grid, b->d_runs, b->d_tasks_f, b->phase_end, b->T_f, b->d_bc_f, b->d_done, R,
+                                   SPIN_LIMIT, 1, b->stream);
+            if (lrc) return bfail(b, OD_ECUDA, "batch tune launch failed");
+            OD_BCK(b, cudaEventRecord(b->e0, b->stream));
+            for (int i = 0; i < reps; ++i)
+                if ((lrc = launch_batch(b->ipt, grid, b->d_runs, b->d_tasks_f, b->phase_end, b->T_f, b->d_bc_f, b->d_done,
+                                        R, SPIN_LIMIT, 1, b->stream)))
+                    return bfail(b, OD_ECUDA, "batch tune launch failed");
+            OD_BCK(b, cudaEventRecord(b->e1, b->stream));
+            OD_BCK(b, cudaEventSynchronize(b->e1));
+            float t = 0.f;
+            OD_BCK(b, cudaEventElapsedTime(&t, b->e0, b->e1));
+            if (ms) ms[a * 3 + c] = t / reps;
+            if (t / reps < best) {
+                best = t / reps;
+                bi = ipts[a];
+                bj = jcs[c];
+            }
+        }
+    b->ipt = bi;
+    b->jc = bj;
+    int rc = batch_build(b);
+    if (rc) return rc;
+    if (best_ipt) *best_ipt = bi;
+    if (best_jc) *best_jc = bj;
+    return OD_OK;
+}
+
+int od_batch_set_config(od_batch* b, int ipt, int jc)
+{
+    if (!b || (ipt != 1 && ipt != 2 && ipt != 4) || jc < 256) return bfail(b, OD_EINVAL, "bad batch configuration");
+    b->ipt = ipt;
+    b->jc = jc;
+    return batch_build(b);
+}
+
+void od_destroy_batch(od_batch* b)
+{
+    if (!b) return;
+    batch_free(b);
+    delete b;
+}
+
+const char* od_batch_last_error(const od_batch* b) { return b ? b->err.c_str() : g_batch_error.c_str(); }
 
 }  // extern "C"

@@ -119,6 +119,30 @@ struct ForceArgs {
     long long U; // units = n_itiles * JS
 };
 
+// One run of a batched launch (od_batch.cu): its parameters, buffers and pair plan.
+struct RunDesc {
+    Phys P;
+    Bufs B;
+    ForceArgs F;
+    int nA;  // scan tiles (256 ions)
+    int nK;  // kick tiles (256 ions)
+};
+
+// Device control block of a batched launch.
+struct BatchCtrl {
+    unsigned long long step;       // batched steps completed
+    unsigned long long task_next;  // monotone task dispenser
+    unsigned exit_count;
+    int err;
+};
+
+constexpr int BATCH_TILE = 256;  // ions per scan / kick tile and threads per CTA of a batch
+ForceArgs batch_plan(int N, int ipt, int jc);
+int batch_blocks_per_sm(int ipt);
+int launch_batch(int ipt, int grid, const RunDesc* runs, const int2* tasks, int4 phase_end, long long T,
+                 BatchCtrl* bc, unsigned long long* done, int R, long long spin_limit, int forces_only,
+                 cudaStream_t s);
+
 // host launchers (od_kernels.cu)
 int launch_init_ions(const Phys& P, const Bufs& B, cudaStream_t s);
 int launch_fpos(const Phys& P, const Bufs& B, int buf, cudaStream_t s);

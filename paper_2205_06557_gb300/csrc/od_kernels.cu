@@ -16,178 +16,9 @@
 #include <mutex>
 #include <string>
 
-#include "od_internal.h"
+#include "od_device.cuh"
 
 namespace od {
-
-// ------------------------------------------------------------------ helpers
-__device__ __forceinline__ float rsqrt_approx(float x)
-{
-    float r;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
-
-__device__ __forceinline__ float ex2_approx(float x)
-{
-    float r;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
-
-__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v)
-{
-    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-
-__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p)
-{
-    unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-
-// Philox4x32-10 (Salmon et al., SC'11): key = seed, counter = (id lo, id hi, word2, stream)
-__device__ __forceinline__ uint4 philox(const Phys& P, unsigned long long id, uint32_t w2, uint32_t stream)
-{
-    uint4 c = make_uint4((uint32_t)id, (uint32_t)(id >> 32), w2, stream);
-    uint32_t k0 = P.key0, k1 = P.key1;
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
-        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
-        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
-    }
-    return c;
-}
-
-// uniform in (0, 1): (w + 1/2) 2^-32
-__device__ __forceinline__ double unif(uint32_t w) { return ((double)w + 0.5) * 2.3283064365386963e-10; }
-
-__device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, double& n0, double& n1)
-{
-    const double rad = sqrt(-2.0 * log(unif(a)));
-    const double t = 6.283185307179586 * unif(b);
-    double s, c;
-    sincos(t, &s, &c);
-    n0 = rad * c;
-    n1 = rad * s;
-}
-
-__device__ __forceinline__ double ncdf(double z) { return 0.5 * erfc(-z * 0.70710678118654752); }
-__device__ __forceinline__ double npdf(double z) { return exp(-0.5 * z * z) * 0.39894228040143268; }
-
-// flux through the bottom face up to axial speed v: int_0^v v' N(v'; u, s^2) dv'
-__device__ double flux_bottom(double v, double u, double s)
-{
-    const double z = (v - u) / s, z0 = -u / s;
-    return u * (ncdf(z) - ncdf(z0)) + s * (npdf(z0) - npdf(z));
-}
-
-// flux through the top face from axial speed v < 0 up to 0: -int_v^0 v' N(v'; u, s^2) dv'
-__device__ double flux_top(double v, double u, double s)
-{
-    const double z = (v - u) / s, z0 = -u / s;
-    return -u * (ncdf(z0) - ncdf(z)) + s * (npdf(z0) - npdf(z));
-}
-
-// Invert a monotone flux CDF F on [lo, hi] for the value target: Newton steps on
-// F(v) - target with derivative |v| N(v; u, s^2), kept inside a shrinking bracket
-// (bisection when a step leaves it).
-template <bool TOP>
-__device__ double invert_flux(double target, double lo, double hi, double v, double u, double s)
-{
-    for (int it = 0; it < 100; ++it) {
-        const double F = TOP ? flux_top(v, u, s) : flux_bottom(v, u, s);
-        const double g = TOP ? (target - F) : (F - target);  // increasing in v
-        if (g < 0) lo = v;
-        else hi = v;
-        const double dg = fabs(v) * npdf((v - u) / s) / s;
-        double vn = dg > 0 ? v - g / dg : 0.5 * (lo + hi);
-        if (!(vn > lo && vn < hi)) vn = 0.5 * (lo + hi);
-        // converged to ~1e-13 of the speed scale (a few hundred ulp above FP64 rounding)
-        const double tol = 1e-13 * fmax(fabs(vn), s);
-        const bool done = fabs(vn - v) <= tol || hi - lo <= tol;
-        v = vn;
-        if (done) break;
-    }
-    return v;
-}
-
-// App. B: face by flux probability, position uniform on the face, flux-weighted velocity
-__device__ void sample_injection(const Phys& P, unsigned long long id, uint32_t sn, Inj& o)
-{
-    const uint4 A = philox(P, id, sn, ST_INJ_A);
-    const uint4 Bw = philox(P, id, sn, ST_INJ_B);
-    double n0, n1;
-    box_muller(Bw.x, Bw.y, n0, n1);
-    if ((unsigned long long)A.x < P.Tbt) {
-        const int f = (unsigned long long)A.x < P.Tb ? 0 : 1;
-        const double rho = P.R * sqrt(unif(A.y));
-        double s, c;
-        sincos(6.283185307179586 * unif(A.z), &s, &c);
-        o.x = rho * c;
-        o.y = rho * s;
-        o.z = f == 0 ? -0.5 * P.H : 0.5 * P.H;
-        o.vx = P.sig * n0;
-        o.vy = P.sig * n1;
-        // flux-weighted axial speed: the tabulated inverse CDF brackets the root and gives
-        // the starting point, Newton polishes it to ~1e-13 (FP64 is slow on this GPU: a
-        // few iterations instead of a bisection from the whole range)
-        const double U = unif(A.w);
-        const double xk = U * VTAB_K;
-        const int k = min((int)xk, VTAB_K - 1);
-        const double* tab = P.vtab + (f == 0 ? 0 : VTAB_K + 1);
-        const double t0 = tab[k], t1 = tab[k + 1];
-        const double pad = 1e-12 * fmax(fmax(fabs(t0), fabs(t1)), P.sig);
-        const double v0 = t0 + (xk - k) * (t1 - t0);
-        if (f == 0)
-            o.vz = invert_flux<false>(U * P.gmax_b, fmax(fmin(t0, t1) - pad, 0.0), fmax(t0, t1) + pad, v0, P.u, P.sig);
-        else
-            o.vz = invert_flux<true>(U * P.gmax_t, fmin(t0, t1) - pad, fmin(fmax(t0, t1) + pad, 0.0), v0, P.u, P.sig);
-        o.face = f;
-    } else {
-        double s, c;
-        sincos(6.283185307179586 * unif(A.y), &s, &c);
-        o.x = P.R * c;
-        o.y = P.R * s;
-        o.z = P.H * (unif(A.z) - 0.5);
-        const double vr = P.sig * sqrt(-2.0 * log(unif(A.w)));  // Rayleigh: flux-weighted radial speed
-        const double vt = (P.flags & OD_F_PAPER_SIDE) ? 0.0 : P.sig * n0;
-        o.vx = -vr * c - vt * s;
-        o.vy = -vr * s + vt * c;
-        o.vz = P.u + P.sig * n1;
-        o.face = 2;
-    }
-    o.id = id;
-}
-
-// E_out = -grad P (App. A): E = (-x G, -y G, -z K), G and K over monomials r2^p z2^q, p+q <= 3
-__device__ __forceinline__ void eout_field(const Phys& P, double x, double y, double z, double& ex, double& ey,
-                                           double& ez)
-{
-    const double r2 = x * x + y * y, z2 = z * z;
-    const double r4 = r2 * r2, z4 = z2 * z2;
-    const double m[10] = {1.0, r2, z2, r4, r2 * z2, z4, r4 * r2, r4 * z2, r2 * z4, z4 * z2};
-    double G = 0.0, K = 0.0;
-#pragma unroll
-    for (int t = 0; t < 10; ++t) {
-        G += P.Gc[t] * m[t];
-        K += P.Kc[t] * m[t];
-    }
-    ex = -x * G;
-    ey = -y * G;
-    ez = -z * K;
-}
-
-__device__ __forceinline__ float4 scaled(const Phys& P, double x, double y, double z, double ls_inv)
-{
-    return make_float4((float)(x * ls_inv), (float)(y * ls_inv), (float)(z * ls_inv), 0.0f);
-}
-
-__device__ __forceinline__ double rnd32(double v) { return (double)(float)v; }
 
 // ------------------------------------------------------------ initial fill
 __global__ void k_init_ions(Phys P, Bufs B, double ls_inv)
@@ -249,550 +80,21 @@ __global__ void k_fpos(Phys P, Bufs B, int buf, double ls_inv)
     }
 }
 
-// ------------------------------------------------- push + scan + compaction
-constexpr int PUSH_BT = 256;
-
-constexpr unsigned FLAG_A = 1u, FLAG_P = 2u;
-
-__device__ __forceinline__ unsigned long long pack_status(uint32_t epoch, unsigned flag, int val)
-{
-    return ((unsigned long long)epoch << 32) | ((unsigned long long)flag << 30) | (unsigned long long)(val & 0x3fffffff);
-}
-
+// ------------------------------------------------------- single-run kernels
 template <int BT>
 __global__ void __launch_bounds__(BT) k_push_scan(Phys P, Bufs B, int n_tiles, double ls_inv)
 {
-    __shared__ unsigned s_tile;
-    __shared__ int s_wsum[BT / 32];
-    __shared__ int s_total, s_prefix, s_last, s_m;
-    __shared__ int s_face[3];
-    Ctrl* C = B.ctrl;
-    const long long step = C->step;
-    const int src = (int)(step & 1), dst = src ^ 1;
-    const uint32_t sn = (uint32_t)(step + 1);
-    const long long cap = B.cap;
-    if (threadIdx.x == 0) s_tile = atomicAdd(&C->tile_counter, 1u);
-    __syncthreads();
-    const int tile = (int)s_tile;
-    const int i = tile * BT + threadIdx.x;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-
-    double x = 0, y = 0, z = 0, vx = 0, vy = 0, vz = 0;
-    unsigned long long id = 0;
-    int cls = -2;  // -2 stays, -1 outflow, k >= 0 absorbed by grain k
-    if (i < P.N) {
-        const double* X = B.x[src];
-        const double* V = B.v[src];
-        x = X[i];
-        y = X[cap + i];
-        z = X[2 * cap + i];
-        vx = V[i];
-        vy = V[cap + i];
-        vz = V[2 * cap + i];
-        id = B.id[src][i];
-        const float4 a = B.acc[i];
-        const double h = 0.5 * P.dt;
-        vx += h * (double)a.x;
-        vy += h * (double)a.y;
-        vz += h * (double)a.z;
-        if (P.flags & OD_F_FP32_STATE) vx = rnd32(vx), vy = rnd32(vy), vz = rnd32(vz);
-        x += P.dt * vx;
-        y += P.dt * vy;
-        z += P.dt * vz;
-        if (P.flags & OD_F_FP32_STATE) x = rnd32(x), y = rnd32(y), z = rnd32(z);
-        if (!isfinite(x + y + z + vx + vy + vz)) atomicOr(&C->err, ERR_NAN);
-        if (!(P.flags & OD_F_NO_ABSORB)) {
-            for (int k = 0; k < P.D; ++k) {
-                const double dx = x - P.gx[k], dy = y - P.gy[k], dz = z - P.gz[k];
-                const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-                if (d2 <= P.ga2[k]) {
-                    cls = k;
-                    break;
-                }
-            }
-        }
-        if (cls == -2 && !(P.flags & OD_F_NO_BOUNDARY)) {
-            const double r2 = __dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y));
-            if (r2 > P.R2 || fabs(z) > P.hz) cls = -1;
-        }
-    }
-    const int removed = cls != -2;
-
-    // event counts with one atomic per warp
-    const unsigned bo = __ballot_sync(0xffffffffu, cls == -1);
-    if (lane == 0 && bo) atomicAdd(&C->ev_step[8], __popc(bo));
-    for (int k = 0; k < P.D; ++k) {
-        const unsigned bk = __ballot_sync(0xffffffffu, cls == k);
-        if (lane == 0 && bk) atomicAdd(&C->ev_step[k], __popc(bk));
-    }
-
-    // block-wide exclusive scan of the removal flags
-    const unsigned bal = __ballot_sync(0xffffffffu, removed);
-    const int wrank = __popc(bal & ((1u << lane) - 1u));
-    if (lane == 0) s_wsum[warp] = __popc(bal);
-    __syncthreads();
-    if (warp == 0) {
-        const int v = lane < BT / 32 ? s_wsum[lane] : 0;
-        int inc = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += t;
-        }
-        if (lane < BT / 32) s_wsum[lane] = inc - v;
-        if (lane == BT / 32 - 1) s_total = inc;
-    }
-    __syncthreads();
-    const int lrank = s_wsum[warp] + wrank;
-
-    // decoupled look-back across tiles (tile ids are taken in launch order, so every
-    // predecessor is running or done); the wait is bounded and reports ERR_TIMEOUT
-    // warp 0 probes 32 predecessors per read: lane l looks at tile base - l
-    if (warp == 0) {
-        const int total = s_total;
-        unsigned long long* st = B.tile_status;
-        int excl = 0;
-        if (tile == 0) {
-            // (the wait self-test withholds tile 0's prefix so that its successors time out)
-            if (lane == 0 && !P.test_hold_tile0) st_release_u64(st, pack_status(sn, FLAG_P, total));
-        } else {
-            if (lane == 0) st_release_u64(st + tile, pack_status(sn, FLAG_A, total));
-            int base = tile - 1;
-            long long spins = 0;
-            unsigned ns = 32;
-            while (true) {
-                const int t = base - lane;
-                unsigned fl = FLAG_P;  // before tile 0: an inclusive prefix of zero
-                int val = 0;
-                if (t >= 0) {
-                    const unsigned long long w = ld_acquire_u64(st + t);
-                    fl = (uint32_t)(w >> 32) == sn ? (unsigned)(w >> 30) & 3u : 0u;
-                    val = (int)(w & 0x3fffffffull);
-                }
-                const unsigned pmask = __ballot_sync(0xffffffffu, fl == FLAG_P);
-                const unsigned zmask = __ballot_sync(0xffffffffu, fl == 0u);
-                const int first_p = pmask ? __ffs(pmask) - 1 : 32;  // nearest inclusive prefix
-                const unsigned need = first_p >= 31 ? 0xffffffffu : ((1u << (first_p + 1)) - 1u);
-                if (zmask & need) {  // a tile up to that prefix has not published yet
-                    if (++spins > P.spin_limit) {
-                        if (lane == 0) atomicOr(&C->err, ERR_TIMEOUT);
-                        break;
-                    }
-                    __nanosleep(ns);
-                    if (ns < 1024) ns *= 2;
-                    continue;
-                }
-                int contrib = lane <= first_p ? val : 0;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) contrib += __shfl_down_sync(0xffffffffu, contrib, o);
-                excl += __shfl_sync(0xffffffffu, contrib, 0);
-                if (first_p < 32) break;
-                base -= 32;
-            }
-            if (lane == 0) st_release_u64(st + tile, pack_status(sn, FLAG_P, excl + total));
-        }
-        if (lane == 0) {
-            // keep destinations in bounds even if a wait gave up
-            if (excl > tile * BT) excl = tile * BT;
-            if (excl < 0) excl = 0;
-            s_prefix = excl;
-            atomicAdd(&C->removed_total, total);
-        }
-    }
-    __syncthreads();
-    const int prefix = s_prefix;
-
-    if (i < P.N) {
-        if (!removed) {
-            const int d = i - prefix - lrank;  // stable compaction
-            double* X = B.x[dst];
-            double* V = B.v[dst];
-            X[d] = x;
-            X[cap + d] = y;
-            X[2 * cap + d] = z;
-            V[d] = vx;
-            V[cap + d] = vy;
-            V[2 * cap + d] = vz;
-            B.id[dst][d] = id;
-            B.fpos[d] = scaled(P, x, y, z, ls_inv);
-        } else {
-            const int r = prefix + lrank;  // global rank among removed ions, index order
-            Rem rm;
-            rm.vx = vx;
-            rm.vy = vy;
-            rm.vz = vz;
-            rm.cls = cls;
-            rm.pad = 0;
-            B.rem[r] = rm;
-            Inj in;
-            sample_injection(P, C->next_id + (unsigned long long)r, sn, in);
-            if (P.flags & OD_F_FP32_STATE) {
-                in.x = rnd32(in.x), in.y = rnd32(in.y), in.z = rnd32(in.z);
-                in.vx = rnd32(in.vx), in.vy = rnd32(in.vy), in.vz = rnd32(in.vz);
-            }
-            in.pad = 0;
-            B.inj[r] = in;
-        }
-    }
-
-    // the last tile to finish places the injected ions at the end, in rank order
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) s_last = atomicAdd(&C->done_counter, 1u) == (unsigned)(n_tiles - 1);
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    if (threadIdx.x < 3) s_face[threadIdx.x] = 0;
-    if (threadIdx.x == 0) {
-        int m = *(volatile int*)&C->removed_total;
-        if (m > P.N) m = P.N;
-        s_m = m;
-    }
-    __syncthreads();
-    const int m = s_m;
-    for (int r = threadIdx.x; r < m; r += BT) {
-        const Inj* in = B.inj + r;
-        const double ix = __ldcg(&in->x), iy = __ldcg(&in->y), iz = __ldcg(&in->z);
-        const double ivx = __ldcg(&in->vx), ivy = __ldcg(&in->vy), ivz = __ldcg(&in->vz);
-        const unsigned long long iid = __ldcg(&in->id);
-        const int face = __ldcg(&in->face);
-        const int d = P.N - m + r;
-        double* X = B.x[dst];
-        double* V = B.v[dst];
-        X[d] = ix;
-        X[cap + d] = iy;
-        X[2 * cap + d] = iz;
-        V[d] = ivx;
-        V[cap + d] = ivy;
-        V[2 * cap + d] = ivz;
-        B.id[dst][d] = iid;
-        B.fpos[d] = scaled(P, ix, iy, iz, ls_inv);
-        atomicAdd(&s_face[face], 1);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        C->ev_step[9] += s_face[0];
-        C->ev_step[10] += s_face[1];
-        C->ev_step[11] += s_face[2];
-        C->next_id += (unsigned long long)m;
-        C->tile_counter = 0u;
-        C->done_counter = 0u;
-    }
+    push_scan_body<BT>(P, B, n_tiles, ls_inv, -1);
 }
 
-// ------------------------------------------------------------ pair forces
-// block g of G owns units [g U / G, (g+1) U / G); this is the block owning unit u
-__device__ __forceinline__ int owner_of(long long u, long long U, int G)
-{
-    return (int)(((u + 1) * (long long)G - 1) / U);
-}
-
-// Scaled coordinates s = r log2(e) / lambda_De make exp(-r/lambda) = 2^-s and
-// 1 + r/lambda = 1 + s ln 2.  Per pair: d = s_j - s_i, r2 = |d|^2 + eps (eps keeps the
-// self pair finite: its d is exactly 0), acc += d (1 + s ln2) 2^-s / s^3.
-template <int BT, int IPT>
-__global__ void __launch_bounds__(BT) k_forces(const float4* __restrict__ fpos, float4* __restrict__ part, ForceArgs F)
-{
-    __shared__ float4 sj[BT];
-    constexpr float EPS2 = 1e-24f;
-    constexpr float LN2 = 0.69314718055994531f;
-    const int g = blockIdx.x;
-    long long u = (long long)g * F.U / F.G;
-    const long long u_end = (long long)(g + 1) * F.U / F.G;
-    while (u < u_end) {
-        const int t = (int)(u / F.JS);
-        const long long u_tile_end = min(u_end, (long long)(t + 1) * F.JS);
-        float xi[IPT], yi[IPT], zi[IPT], ax[IPT], ay[IPT], az[IPT];
-#pragma unroll
-        for (int k = 0; k < IPT; ++k) {
-            const float4 p = fpos[t * F.TI + k * BT + threadIdx.x];
-            xi[k] = p.x;
-            yi[k] = p.y;
-            zi[k] = p.z;
-            ax[k] = 0.f;
-            ay[k] = 0.f;
-            az[k] = 0.f;
-        }
-        for (; u < u_tile_end; ++u) {
-            const int c = (int)(u % F.JS);
-            const int j0 = c * F.JC;
-            const int j1 = min(j0 + F.JC, F.n_pad);
-            for (int jb = j0; jb < j1; jb += BT) {
-                __syncthreads();
-                sj[threadIdx.x] = fpos[jb + threadIdx.x];
-                __syncthreads();
-#pragma unroll 8
-                for (int jj = 0; jj < BT; ++jj) {
-                    const float4 pj = sj[jj];
-#pragma unroll
-                    for (int k = 0; k < IPT; ++k) {
-                        const float dx = pj.x - xi[k], dy = pj.y - yi[k], dz = pj.z - zi[k];
-                        float r2 = fmaf(dx, dx, EPS2);
-                        r2 = fmaf(dy, dy, r2);
-                        r2 = fmaf(dz, dz, r2);
-                        const float ri = rsqrt_approx(r2);
-                        const float s = r2 * ri;
-                        const float e = ex2_approx(-s);
-                        const float f = fmaf(s, LN2, 1.0f);
-                        const float c3 = (f * e) * (ri * ri * ri);
-                        ax[k] = fmaf(c3, dx, ax[k]);
-                        ay[k] = fmaf(c3, dy, ay[k]);
-                        az[k] = fmaf(c3, dz, az[k]);
-                    }
-                }
-            }
-        }
-        const int slot = g - owner_of((long long)t * F.JS, F.U, F.G);
-        float4* out = part + (long long)slot * F.n_pad + t * F.TI + threadIdx.x;
-#pragma unroll
-        for (int k = 0; k < IPT; ++k) out[k * BT] = make_float4(ax[k], ay[k], az[k], 0.f);
-    }
-}
-
-// ---------------------------------------------- kick, collisions, grain sums
-constexpr int KICK_BT = 64;  // small blocks spread small runs over many SMs (FP64 is slow)
-
-__device__ __forceinline__ double warp_sum(double v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// mode 0: after the push (second half kick + collisions); mode 1: forces only (creation
-// or a replaced ion state)
 template <int BT>
 __global__ void __launch_bounds__(BT) k_kick(Phys P, Bufs B, ForceArgs F, int mode)
 {
-    __shared__ double s_red[BT / 32][3];
-    Ctrl* C = B.ctrl;
-    const long long step = C->step;
-    const int buf = mode == 0 ? (int)((step + 1) & 1) : (int)(step & 1);
-    const uint32_t sn = (uint32_t)(step + 1);
-    const int i = blockIdx.x * BT + threadIdx.x;
-    const bool live = i < P.N;
-    const long long cap = B.cap;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    double x = 0, y = 0, z = 0;
-    int coll = 0;
-    if (live) {
-        const double* X = B.x[buf];
-        x = X[i];
-        y = X[cap + i];
-        z = X[2 * cap + i];
-        float ax = 0.f, ay = 0.f, az = 0.f;
-        if (!(P.flags & OD_F_NO_IONION)) {
-            const int t = i / F.TI;
-            const long long u0 = (long long)t * F.JS;
-            const int g0 = owner_of(u0, F.U, F.G), g1 = owner_of(u0 + F.JS - 1, F.U, F.G);
-#pragma unroll 8
-            for (int s = 0; s <= g1 - g0; ++s) {
-                const float4 p = __ldcs(B.part + (long long)s * F.n_pad + i);
-                ax += p.x;
-                ay += p.y;
-                az += p.z;
-            }
-            ax *= -P.k_ii;
-            ay *= -P.k_ii;
-            az *= -P.k_ii;
-        }
-        // bare Coulomb force of the grains (asymmetric model): FP32 terms from FP64
-        // separations, like the pair forces
-        for (int k = 0; k < P.D; ++k) {
-            const float dx = (float)(x - P.gx[k]), dy = (float)(y - P.gy[k]), dz = (float)(z - P.gz[k]);
-            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            const float ri = rsqrt_approx(r2);
-            const float c = (float)(P.kdi * C->Q[k]) * (ri * ri * ri);
-            ax = fmaf(c, dx, ax);
-            ay = fmaf(c, dy, ay);
-            az = fmaf(c, dz, az);
-        }
-        // E_out (FP64 polynomial) and the driving field
-        double bx = 0.0, by = 0.0, bz = P.qm * P.E;
-        if (P.eout) {
-            double ex, ey, ez;
-            eout_field(P, x, y, z, ex, ey, ez);
-            bx += P.qm * ex;
-            by += P.qm * ey;
-            bz += P.qm * ez;
-        }
-        const float4 a = make_float4((float)((double)ax + bx), (float)((double)ay + by), (float)((double)az + bz), 0.f);
-        B.acc[i] = a;
-        if (mode == 0) {
-            double* V = B.v[buf];
-            double vx = V[i], vy = V[cap + i], vz = V[2 * cap + i];
-            const double h = 0.5 * P.dt;
-            vx += h * (double)a.x;
-            vy += h * (double)a.y;
-            vz += h * (double)a.z;
-            // Andersen collision with the neutrals: integer threshold on a Philox word
-            const unsigned long long id = B.id[buf][i];
-            const uint4 w = philox(P, id, sn, ST_COLL);
-            if ((unsigned long long)w.x < P.Tcoll) {
-                const uint4 wv = philox(P, id, sn, ST_COLL_VEL);
-                double n0, n1, n2, n3;
-                box_muller(wv.x, wv.y, n0, n1);
-                box_muller(wv.z, wv.w, n2, n3);
-                vx = P.sig_n * n0;
-                vy = P.sig_n * n1;
-                vz = P.sig_n * n2;
-                coll = 1;
-            }
-            if (P.flags & OD_F_FP32_STATE) vx = rnd32(vx), vy = rnd32(vy), vz = rnd32(vz);
-            V[i] = vx;
-            V[cap + i] = vy;
-            V[2 * cap + i] = vz;
-        }
-    }
-    const unsigned bc = __ballot_sync(0xffffffffu, coll);
-    if (lane == 0 && bc) atomicAdd(&C->ev_step[12], __popc(bc));
-
-    // grain side of Eq. 1 without the prefactor q Q_k / (4 pi eps0):
-    // sum_i (1 + rho/lambda) exp(-rho/lambda) (r_k - r_i) / rho^3; FP32 terms from FP64
-    // separations, FP64 sums in a fixed order (warp tree, then block tree)
-    const float lam_inv = (float)P.lam_inv;
-    const float lam_inv_l2 = (float)(P.lam_inv * 1.4426950408889634);
-    for (int k = 0; k < P.D; ++k) {
-        double fx = 0.0, fy = 0.0, fz = 0.0;
-        if (live) {
-            const float dx = (float)(P.gx[k] - x), dy = (float)(P.gy[k] - y), dz = (float)(P.gz[k] - z);
-            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            const float ri = rsqrt_approx(r2);
-            const float rho = r2 * ri;
-            const float f = fmaf(rho, lam_inv, 1.0f) * ex2_approx(-rho * lam_inv_l2) * (ri * ri * ri);
-            fx = (double)(f * dx);
-            fy = (double)(f * dy);
-            fz = (double)(f * dz);
-        }
-        fx = warp_sum(fx);
-        fy = warp_sum(fy);
-        fz = warp_sum(fz);
-        if (lane == 0) {
-            s_red[warp][0] = fx;
-            s_red[warp][1] = fy;
-            s_red[warp][2] = fz;
-        }
-        __syncthreads();
-        if (warp == 0) {
-            double a0 = lane < BT / 32 ? s_red[lane][0] : 0.0;
-            double a1 = lane < BT / 32 ? s_red[lane][1] : 0.0;
-            double a2 = lane < BT / 32 ? s_red[lane][2] : 0.0;
-            a0 = warp_sum(a0);
-            a1 = warp_sum(a1);
-            a2 = warp_sum(a2);
-            if (lane == 0) {
-                double* o = B.dpart + ((long long)blockIdx.x * MAXD + k) * 3;
-                o[0] = a0;
-                o[1] = a1;
-                o[2] = a2;
-            }
-        }
-        __syncthreads();
-    }
+    kick_body<BT>(P, B, F, mode, blockIdx.x);
 }
 
-// --------------------------------------------------------------- grain tail
-constexpr int DUST_BT = 256;
+__global__ void __launch_bounds__(DUST_BT) k_dust(Phys P, Bufs B, int nb, int mode) { dust_body(P, B, nb, mode); }
 
-__global__ void __launch_bounds__(DUST_BT) k_dust(Phys P, Bufs B, int nb, int mode)
-{
-    __shared__ double s_S[MAXD][3];
-    __shared__ double s_rec[MAXD][REC];
-    Ctrl* C = B.ctrl;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // deterministic reduction of the kick kernel's per-block grain sums: warp w takes
-    // component pairs w, w+8, ...; lanes stride the blocks, then a fixed shuffle tree
-    for (int pc = warp; pc < P.D * 3; pc += DUST_BT / 32) {
-        const int k = pc / 3, c = pc % 3;
-        double s = 0.0;
-        for (int b = lane; b < nb; b += 32) s += B.dpart[((long long)b * MAXD + k) * 3 + c];
-        s = warp_sum(s);
-        if (lane == 0) s_S[k][c] = s;
-    }
-    __syncthreads();
-    const int k = threadIdx.x;
-    if (k < P.D) {
-        const double Q = C->Q[k];
-        double ex = 0.0, ey = 0.0, ez = 0.0;
-        if (P.eout) eout_field(P, P.gx[k], P.gy[k], P.gz[k], ex, ey, ez);
-        const double c = P.korb * Q;
-        const double fo[3] = {c * s_S[k][0] + ex * Q, c * s_S[k][1] + ey * Q, c * s_S[k][2] + ez * Q};
-        for (int j = 0; j < 3; ++j) C->f_orbit[k][j] = fo[j];
-        if (mode == 0) {
-            // Eq. 2: Coulomb force of the other grains
-            double fdd[3] = {0.0, 0.0, 0.0};
-            for (int p = 0; p < P.D; ++p) {
-                if (p == k) continue;
-                const double dx = P.gx[k] - P.gx[p], dy = P.gy[k] - P.gy[p], dz = P.gz[k] - P.gz[p];
-                const double d = sqrt(dx * dx + dy * dy + dz * dz);
-                const double cc = P.inv4pieps0 * Q * C->Q[p] / (d * d * d);
-                fdd[0] += cc * dx;
-                fdd[1] += cc * dy;
-                fdd[2] += cc * dz;
-            }
-            // Eq. 3: momentum of the ions absorbed this step, summed in index order
-            const int m = C->removed_total;
-            double pm[3] = {0.0, 0.0, 0.0};
-            for (int r = 0; r < m; ++r) {
-                const Rem rm = B.rem[r];
-                if (rm.cls == k) {
-                    pm[0] += P.m * rm.vx;
-                    pm[1] += P.m * rm.vy;
-                    pm[2] += P.m * rm.vz;
-                }
-            }
-            for (int j = 0; j < 3; ++j) {
-                s_rec[k][1 + j] = fo[j];
-                s_rec[k][4 + j] = fdd[j];
-                s_rec[k][7 + j] = pm[j] / P.dt;
-            }
-            s_rec[k][10] = 0.0;
-            s_rec[k][11] = 0.0;
-            s_rec[k][12] = Q * P.E;  // Eq. 4
-        }
-    }
-    __syncthreads();
-    if (mode != 0) return;
-    const long long step = C->step;
-    const long long sn = step + 1;
-    if (k < P.D) {
-        double Q = C->Q[k];
-        if (P.charge_model == OD_Q_CONSISTENT) {
-            // absorbed superions plus the OML electron flux at the isolated-sphere potential
-            const double a = P.ga[k];
-            const double xe = Q * P.inv4pieps0 / a * P.e_over_kTe;
-            const double fac = xe <= 0.0 ? exp(xe) : 1.0 + xe;
-            const double flux = 4.0 * 3.141592653589793 * a * a * P.Ie0 * fac;
-            Q = Q + P.q * (double)C->ev_step[k] - 1.602176634e-19 * flux * P.dt;
-            C->Q[k] = Q;
-        }
-        s_rec[k][0] = Q;
-        if (step < C->series_cap) {
-            double* o = C->series + (step * MAXD + k) * REC;
-            for (int j = 0; j < REC; ++j) o[j] = s_rec[k][j];
-        }
-        if (sn >= P.avg_start)
-            for (int j = 0; j < REC; ++j) C->wsum[k][j] += s_rec[k][j];
-    }
-    __syncthreads();
-    // one thread per event counter: record, accumulate, reset for the next step
-    const int j = threadIdx.x;
-    if (j < EV) {
-        const int e = C->ev_step[j];
-        if (step < C->series_cap) C->evseries[step * EV + j] = e;
-        C->counters[j] += e;
-        C->ev_step[j] = 0;
-    } else if (j == 32) {
-        C->counters[13] = sn;
-        C->counters[14] = P.N;
-        C->counters[15] = (long long)C->next_id;
-        if (sn >= P.avg_start) C->wcount += 1;
-        C->removed_total = 0;
-        C->step = sn;
-    }
-}
-
-// window means and batch-means standard errors (20 batches) of every record entry
 __global__ void k_stats(Phys P, Bufs B, double* out)
 {
     const Ctrl* C = B.ctrl;
@@ -1100,3 +402,4 @@ extern "C" int od_pair_accel_static(const double* x, int64_t n, double lambda_De
     }
     return OD_OK;
 }
+
