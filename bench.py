@@ -40,7 +40,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="scale", choices=["scale", "tiny", "chain"])
+    ap.add_argument("--workload", default="scale", choices=["scale", "tiny", "chain", "sweep"])
+    ap.add_argument("--runs", type=int, default=64)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -181,7 +182,7 @@ def run_ours(args):
     N = run.N
     info = run.info()
     # pair-kernel autotuner (untimed; cached per device and ion count)
-    tv, tg, _ = od.tune_cached(run.h, "%s|N=%d" % (torch.cuda.get_device_name(local), N))
+    tv, tg, tb, _ = od.tune_cached(run.h, "%s|N=%d" % (torch.cuda.get_device_name(local), N))
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
 
     for _ in range(args.warmup):
@@ -256,7 +257,8 @@ def run_ours(args):
                    "l2": "flushed between timed steps (256 MB write)", "parallelism": "replicas" if world > 1 else "1 GPU",
                    "precision": "pair forces FP32; ion state, grain sums and averages FP64",
                    "pair_kernel": {"threads": od.force_variant_shape(tv)[0], "targets_per_thread":
-                                   od.force_variant_shape(tv)[1], "units_per_block": tg}},
+                                   od.force_variant_shape(tv)[1], "units_per_block": tg,
+                                   "ctas_per_sm": tb or "occupancy limit"}},
         "ion_steps_per_s": world * float(N) * args.steps / (t_max / 1e3),
         "wall_s_timed": wall,
         "kernel_ms_per_step": {"push_scan_inject": kms[0] / max(kn[0], 1), "pair_forces": k1_ms,
@@ -277,6 +279,53 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_sweep(args):
+    """64 independent runs (N log-uniform in [1e4, 2e5], Mach U(0.3, 2), 1-4 grains):
+    one batched launch per step against the same runs stepped one after another."""
+    import torch
+
+    import paper_2205_06557_gb300 as od
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    plist = [W.sweep_run(rank * 1000 + s) for s in range(args.runs)]
+    batch = od.Batch(plist, stream=ctypes_stream(stream))
+    Ns = np.array([r.N for r in batch.runs], dtype=np.float64)
+    pairs_step = float((Ns * (Ns - 1)).sum())
+    _, ipt, jc = batch.tune(reps=1)
+    batch.step(args.warmup)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    batch.step(args.steps)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    batch.close()
+    # the same runs one after another, each with its own tuned pair kernel
+    t_seq = 0.0
+    for p in plist:
+        run = od.Run(p, stream=ctypes_stream(stream))
+        od.od_tune(run.h, reps=1)
+        run.step(args.warmup)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        run.step(args.steps)
+        torch.cuda.synchronize()
+        t_seq += time.perf_counter() - t0
+        run.close()
+    line = {"metric": METRIC, "value": pairs_step * args.steps / t_batch, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_batch / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "sweep of %d independent runs, N log-uniform in [1e4, 2e5] (total %d ions), "
+                                   "Mach U(0.3, 2), 1-4 grains" % (args.runs, int(Ns.sum())),
+                       "batch_pair_tasks": {"targets_per_thread": ipt, "source_chunk": jc}},
+            "sequential": {"value": pairs_step * args.steps / t_seq, "ms_per_step": 1e3 * t_seq / args.steps},
+            "batch_speedup": t_seq / t_batch, "ion_steps_per_s": float(Ns.sum()) * args.steps / t_batch}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def ctypes_stream(stream):
     h = stream.cuda_stream
     return h if h else None
@@ -286,6 +335,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "sweep":
+        run_sweep(args)
     else:
         run_ours(args)
 

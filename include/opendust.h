@@ -156,15 +156,16 @@ int od_kernel_times(od_handle* h, double* ms, int64_t* launches);
 
 /* Pair-kernel autotuner (the all-pairs force evaluation of Sec. 5 is the hot spot).
  * od_tune times every kernel variant (threads per block x targets per thread) at four
- * work granularities (4, 8, 16, 32 units per persistent block) on the run's current
- * ions, reps launches each, keeps the fastest and writes the average ms per launch
- * to ms[n_variants * 4] (host, may be NULL; row = variant, column = granularity).
- * od_set_force_config applies a known choice (e.g. from a cache) and
- * od_get_force_config reports the current one and the number of variants.  The ion
- * state is not changed; call between steps. */
-int od_tune(od_handle* h, int reps, double* ms, int* best_variant, int* best_units_per_block);
-int od_set_force_config(od_handle* h, int variant, int units_per_block);
-int od_get_force_config(od_handle* h, int* variant, int* units_per_block, int* n_variants);
+ * work granularities (4, 8, 16, 32 units per persistent block) and three persistent
+ * grid sizes (CTAs per SM: the occupancy limit, 4, 2) on the run's current ions, reps
+ * launches each, keeps the fastest and writes the average ms per launch to
+ * ms[n_variants][4][3] (host, may be NULL; -1 where a cap is not below the limit).
+ * od_set_force_config applies a known choice (e.g. from a cache; blocks_per_sm 0 =
+ * occupancy limit) and od_get_force_config reports the current one and the number of
+ * variants.  The ion state is not changed; call between steps. */
+int od_tune(od_handle* h, int reps, double* ms, int* best_variant, int* best_units_per_block, int* best_blocks_per_sm);
+int od_set_force_config(od_handle* h, int variant, int units_per_block, int blocks_per_sm);
+int od_get_force_config(od_handle* h, int* variant, int* units_per_block, int* blocks_per_sm, int* n_variants);
 
 /* ---- batches: many independent runs in one launch per step ----
  * The paper's sweeps (Sec. 4: drag versus Mach number, versus collision frequency)

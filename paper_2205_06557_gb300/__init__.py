@@ -98,9 +98,9 @@ def lib():
         L.od_last_error.restype = ctypes.c_char_p
         L.od_pair_accel_static.argtypes = [vp, i64, ctypes.c_double, ctypes.c_double, vp, vp]
         L.od_pair_accel_static.restype = ctypes.c_int
-        L.od_tune.argtypes = [vp, ctypes.c_int, vp, vp, vp]
-        L.od_set_force_config.argtypes = [vp, ctypes.c_int, ctypes.c_int]
-        L.od_get_force_config.argtypes = [vp, vp, vp, vp]
+        L.od_tune.argtypes = [vp, ctypes.c_int, vp, vp, vp, vp]
+        L.od_set_force_config.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        L.od_get_force_config.argtypes = [vp, vp, vp, vp, vp]
         L.od_selftest_wait_timeout.argtypes = [vp, i64]
         L.od_create_batch.argtypes = [vp, i32, P(vp)]
         L.od_batch_step.argtypes = [vp, i64]
@@ -279,22 +279,23 @@ def force_variant_shape(v):
 
 
 def od_get_force_config(h):
-    v, g, nv = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-    _check(lib().od_get_force_config(h, ctypes.byref(v), ctypes.byref(g), ctypes.byref(nv)), h)
-    return v.value, g.value, nv.value
+    """(variant, units_per_block, blocks_per_sm, n_variants)"""
+    v, g, b, nv = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().od_get_force_config(h, ctypes.byref(v), ctypes.byref(g), ctypes.byref(b), ctypes.byref(nv)), h)
+    return v.value, g.value, b.value, nv.value
 
 
-def od_set_force_config(h, variant, units_per_block):
-    return _check(lib().od_set_force_config(h, int(variant), int(units_per_block)), h)
+def od_set_force_config(h, variant, units_per_block, blocks_per_sm=0):
+    return _check(lib().od_set_force_config(h, int(variant), int(units_per_block), int(blocks_per_sm)), h)
 
 
 def od_tune(h, reps=3):
-    """time every pair-kernel configuration; returns (ms[n_variants, 4], best_variant, best_upb)"""
-    nv = od_get_force_config(h)[2]
-    ms = np.zeros((nv, 4))
-    bv, bg = ctypes.c_int(), ctypes.c_int()
-    _check(lib().od_tune(h, int(reps), _ptr(ms), ctypes.byref(bv), ctypes.byref(bg)), h)
-    return ms, bv.value, bg.value
+    """time every pair-kernel configuration; returns (ms[n_variants, 4, 3], variant, upb, bps)"""
+    nv = od_get_force_config(h)[3]
+    ms = np.zeros((nv, 4, 3))
+    bv, bg, bb = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().od_tune(h, int(reps), _ptr(ms), ctypes.byref(bv), ctypes.byref(bg), ctypes.byref(bb)), h)
+    return ms, bv.value, bg.value, bb.value
 
 
 def _tune_cache_path():
@@ -312,12 +313,12 @@ def tune_cached(h, key, reps=3, path=None):
         cache = json.load(open(path))
     except (OSError, ValueError):
         cache = {}
-    if key in cache:
-        v, g = cache[key]
-        od_set_force_config(h, v, g)
-        return v, g, None
-    ms, v, g = od_tune(h, reps)
-    cache[key] = [v, g]
+    if key in cache and len(cache[key]) == 3:
+        v, g, b = cache[key]
+        od_set_force_config(h, v, g, b)
+        return v, g, b, None
+    ms, v, g, b = od_tune(h, reps)
+    cache[key] = [v, g, b]
     try:
         os.makedirs(os.path.dirname(path), exist_ok=True)
         tmp = path + ".tmp%d" % os.getpid()
@@ -325,7 +326,7 @@ def tune_cached(h, key, reps=3, path=None):
         os.replace(tmp, path)
     except OSError:
         pass
-    return v, g, ms
+    return v, g, b, ms
 
 
 STATIC_MAX_IONS = 32768

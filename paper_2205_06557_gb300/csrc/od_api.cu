@@ -175,6 +175,7 @@ struct od_handle {
     ForceArgs F{};
     int variant = 0;
     int upb = 8;  // pair-kernel work units per persistent block
+    int bps = 0;  // persistent pair-kernel CTAs per SM (0 = occupancy limit)
     bool batch_member = false;  // stepped only through its batch (od_batch_step)
     cudaStream_t stream = nullptr;
     bool own_stream = false;
@@ -421,7 +422,7 @@ int build_eout(od_handle* h, const od_params* p)
 }
 
 // balanced partition of the all-pairs work for pair-kernel variant v
-ForceArgs plan_forces(int N, int v, int sms, int units_per_block)
+ForceArgs plan_forces(int N, int v, int sms, int units_per_block, int bps_cap)
 {
     ForceArgs F{};
     const ForceVariant fv = force_variant(v);
@@ -429,7 +430,8 @@ ForceArgs plan_forces(int N, int v, int sms, int units_per_block)
     F.n_pad = N == 0 ? 0 : (N + F.TI - 1) / F.TI * F.TI;
     if (F.n_pad == 0) return F;
     const int n_it = F.n_pad / F.TI;
-    const long long gmax = (long long)sms * force_blocks_per_sm(v);
+    const int occ = force_blocks_per_sm(v);
+    const long long gmax = (long long)sms * (bps_cap > 0 ? std::min(bps_cap, occ) : occ);
     long long js = (units_per_block * gmax + n_it - 1) / n_it;
     js = std::max(1ll, std::min(js, (long long)F.n_pad / fv.BT));
     long long jc = ((F.n_pad + js - 1) / js + fv.BT - 1) / fv.BT * fv.BT;
@@ -469,7 +471,7 @@ int replan(od_handle* h, int N)
 {
     h->P.N = N;
     if (h->variant < 0 || h->variant >= num_force_variants()) h->variant = default_variant(N);
-    h->F = plan_forces(N, h->variant, h->sms, h->upb);
+    h->F = plan_forces(N, h->variant, h->sms, h->upb, h->bps);
     h->P.n_pad = h->F.n_pad;
     if (h->F.n_pad > h->npad_cap) return fail(h, OD_EOVERFLOW, "padded ion count exceeds the buffer");
     return ensure_part(h);
@@ -911,11 +913,13 @@ int od_kernel_times(od_handle* h, double* ms, int64_t* launches)
 const char* od_last_error(const od_handle* h) { return h ? h->err.c_str() : g_create_error.c_str(); }
 
 static const int kTuneGrains[4] = {4, 8, 16, 32};
+static const int kTuneBps[3] = {0, 4, 2};  // persistent CTAs per SM: 0 = occupancy limit
 
-static int apply_force_config(od_handle* h, int variant, int upb)
+static int apply_force_config(od_handle* h, int variant, int upb, int bps)
 {
     h->variant = variant;
     h->upb = upb;
+    h->bps = bps;
     int rc = replan(h, h->P.N);
     if (rc) return rc;
     h->graph_ok = false;
@@ -924,51 +928,55 @@ static int apply_force_config(od_handle* h, int variant, int upb)
     return OD_OK;
 }
 
-int od_set_force_config(od_handle* h, int variant, int units_per_block)
+int od_set_force_config(od_handle* h, int variant, int units_per_block, int blocks_per_sm)
 {
     if (!h || variant < 0 || variant >= num_force_variants() || units_per_block < 1 || units_per_block > 1024 ||
-        h->batch_member)
+        blocks_per_sm < 0 || blocks_per_sm > 64 || h->batch_member)
         return fail(h, OD_EINVAL, "bad force configuration (or a batch member: use od_batch_set_config)");
-    int rc = apply_force_config(h, variant, units_per_block);
+    int rc = apply_force_config(h, variant, units_per_block, blocks_per_sm);
     if (rc) return rc;
     OD_CK(h, cudaStreamSynchronize(h->stream));
     return OD_OK;
 }
 
-int od_tune(od_handle* h, int reps, double* ms, int* best_variant, int* best_upb)
+int od_tune(od_handle* h, int reps, double* ms, int* best_variant, int* best_upb, int* best_bps)
 {
     if (!h || reps < 1 || h->batch_member)
         return fail(h, OD_EINVAL, "bad handle or repetition count (or a batch member: use od_batch_tune)");
     const int nv = num_force_variants();
     if (ms)
-        for (int i = 0; i < nv * 4; ++i) ms[i] = -1.0;
+        for (int i = 0; i < nv * 4 * 3; ++i) ms[i] = -1.0;
     if (h->P.N == 0 || (h->P.flags & OD_F_NO_IONION)) {
         if (best_variant) *best_variant = h->variant;
         if (best_upb) *best_upb = h->upb;
+        if (best_bps) *best_bps = h->bps;
         return OD_OK;
     }
     double best = 1e300;
-    int bv = h->variant, bg = h->upb;
+    int bv = h->variant, bg = h->upb, bb = h->bps;
     for (int v = 0; v < nv; ++v)
-        for (int g = 0; g < 4; ++g) {
-            int rc = apply_force_config(h, v, kTuneGrains[g]);
-            if (rc) return rc;
-            OD_LK(h, launch_forces(h->P, h->B, h->F, h->variant, h->stream));
-            OD_CK(h, cudaEventRecord(h->ev[0], h->stream));
-            for (int r = 0; r < reps; ++r) OD_LK(h, launch_forces(h->P, h->B, h->F, h->variant, h->stream));
-            OD_CK(h, cudaEventRecord(h->ev[1], h->stream));
-            OD_CK(h, cudaEventSynchronize(h->ev[1]));
-            float t = 0.f;
-            OD_CK(h, cudaEventElapsedTime(&t, h->ev[0], h->ev[1]));
-            const double avg = t / reps;
-            if (ms) ms[v * 4 + g] = avg;
-            if (avg < best) {
-                best = avg;
-                bv = v;
-                bg = kTuneGrains[g];
+        for (int g = 0; g < 4; ++g)
+            for (int c = 0; c < 3; ++c) {
+                if (kTuneBps[c] >= force_blocks_per_sm(v)) continue;  // no cap below the occupancy limit
+                int rc = apply_force_config(h, v, kTuneGrains[g], kTuneBps[c]);
+                if (rc) return rc;
+                OD_LK(h, launch_forces(h->P, h->B, h->F, h->variant, h->stream));
+                OD_CK(h, cudaEventRecord(h->ev[0], h->stream));
+                for (int r = 0; r < reps; ++r) OD_LK(h, launch_forces(h->P, h->B, h->F, h->variant, h->stream));
+                OD_CK(h, cudaEventRecord(h->ev[1], h->stream));
+                OD_CK(h, cudaEventSynchronize(h->ev[1]));
+                float t = 0.f;
+                OD_CK(h, cudaEventElapsedTime(&t, h->ev[0], h->ev[1]));
+                const double avg = t / reps;
+                if (ms) ms[(v * 4 + g) * 3 + c] = avg;
+                if (avg < best) {
+                    best = avg;
+                    bv = v;
+                    bg = kTuneGrains[g];
+                    bb = kTuneBps[c];
+                }
             }
-        }
-    int rc = apply_force_config(h, bv, bg);
+    int rc = apply_force_config(h, bv, bg, bb);
     if (rc) return rc;
     // the last force evaluation's partial sums belong to the configuration just left:
     // recompute them for the chosen one so the next kick reads a consistent layout
@@ -976,6 +984,7 @@ int od_tune(od_handle* h, int reps, double* ms, int* best_variant, int* best_upb
     OD_CK(h, cudaStreamSynchronize(h->stream));
     if (best_variant) *best_variant = bv;
     if (best_upb) *best_upb = bg;
+    if (best_bps) *best_bps = bb;
     return read_error_word(h);
 }
 
@@ -992,11 +1001,12 @@ int od_selftest_wait_timeout(od_handle* h, int64_t polls)
     return read_error_word(h);
 }
 
-int od_get_force_config(od_handle* h, int* variant, int* units_per_block, int* n_variants)
+int od_get_force_config(od_handle* h, int* variant, int* units_per_block, int* blocks_per_sm, int* n_variants)
 {
     if (!h) return fail(h, OD_EINVAL, "bad handle");
     if (variant) *variant = h->variant;
     if (units_per_block) *units_per_block = h->upb;
+    if (blocks_per_sm) *blocks_per_sm = h->bps;
     if (n_variants) *n_variants = num_force_variants();
     return OD_OK;
 }

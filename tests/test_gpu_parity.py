@@ -278,9 +278,9 @@ def test_tuned_configuration_keeps_results():
     p = W.tiny()
     ref = od.Run(p)
     tuned = od.Run(p)
-    ms, v, g = od.od_tune(tuned.h, reps=1)
-    assert ms[v, [4, 8, 16, 32].index(g)] == ms[ms > 0].min()
-    assert od.od_get_force_config(tuned.h)[:2] == (v, g)
+    ms, v, g, b = od.od_tune(tuned.h, reps=1)
+    assert ms[v, [4, 8, 16, 32].index(g), [0, 4, 2].index(b)] == ms[ms > 0].min()
+    assert od.od_get_force_config(tuned.h)[:3] == (v, g, b)
     ref.step(20)
     tuned.step(20)
     _, ev_r = ref.series(1, 20)
