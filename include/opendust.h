@@ -193,6 +193,30 @@ int od_batch_set_config(od_batch* b, int targets_per_thread, int chunk);
 void od_destroy_batch(od_batch* b);
 const char* od_batch_last_error(const od_batch* b);
 
+/* ---- learned warm start for the self-consistent charge (no counterpart in the paper) ----
+ * A set-pooled MLP maps (Mach number, collision frequency, T_e/T_i; per grain position and
+ * radius) to per-grain (charge, force) in normalised units; its prediction only seeds the
+ * charges q0 of a run with the "consistent" model (Sec. 2), and the method itself then
+ * converges and judges the result.  Layers: per grain 7 -> 256 -> 256 (relu), masked mean
+ * over the sample's grains, [h, mean] 512 -> 256 -> 256 (relu) -> 4.  FP32 master weights
+ * with Adam; every product uses BF16 weights and activations with FP32 accumulation on
+ * the tensor cores.  Inputs are host arrays: x[B][8][7], mask[B][8] (1 present, 0 absent),
+ * targets[B][8][4]; B <= max_batch.  Parameters are flattened layer by layer as W
+ * (out x in, row-major, in padded to 16 for the first layer, out padded to 16 for the last)
+ * followed by b (out).  stream: cudaStream_t (NULL = legacy default stream). */
+typedef struct od_sur od_sur;
+int od_sur_create(int max_batch, uint64_t seed, void* stream, od_sur** out);
+void od_sur_destroy(od_sur* s);
+int od_sur_num_params(const od_sur* s);
+int od_sur_get_params(od_sur* s, float* params);
+int od_sur_set_params(od_sur* s, const float* params);
+int od_sur_forward(od_sur* s, const float* x, const float* mask, int B, float* y);
+int od_sur_gradients(od_sur* s, const float* x, const float* mask, const float* targets, int B, double* loss,
+                     float* grads);
+int od_sur_train_step(od_sur* s, const float* x, const float* mask, const float* targets, int B, float lr,
+                      double* loss);
+const char* od_sur_last_error(const od_sur* s);
+
 /* Failure-detection self-test (no counterpart in the paper): runs one push/scan kernel in
  * which the first scan tile withholds its prefix, so the look-back wait of the next
  * tile finds no inclusive prefix and gives up after `polls` polls instead of its usual

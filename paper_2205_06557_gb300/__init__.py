@@ -115,6 +115,20 @@ def lib():
         L.od_batch_last_error.restype = ctypes.c_char_p
         for name in ("od_create_batch", "od_batch_step", "od_batch_size", "od_batch_tune", "od_batch_set_config"):
             getattr(L, name).restype = ctypes.c_int
+        L.od_sur_create.argtypes = [ctypes.c_int, ctypes.c_uint64, vp, P(vp)]
+        L.od_sur_destroy.argtypes = [vp]
+        L.od_sur_destroy.restype = None
+        L.od_sur_num_params.argtypes = [vp]
+        L.od_sur_get_params.argtypes = [vp, vp]
+        L.od_sur_set_params.argtypes = [vp, vp]
+        L.od_sur_forward.argtypes = [vp, vp, vp, ctypes.c_int, vp]
+        L.od_sur_gradients.argtypes = [vp, vp, vp, vp, ctypes.c_int, vp, vp]
+        L.od_sur_train_step.argtypes = [vp, vp, vp, vp, ctypes.c_int, ctypes.c_float, vp]
+        L.od_sur_last_error.argtypes = [vp]
+        L.od_sur_last_error.restype = ctypes.c_char_p
+        for name in ("od_sur_create", "od_sur_num_params", "od_sur_get_params", "od_sur_set_params", "od_sur_forward",
+                     "od_sur_gradients", "od_sur_train_step"):
+            getattr(L, name).restype = ctypes.c_int
         for name in ("od_tune", "od_set_force_config", "od_get_force_config", "od_selftest_wait_timeout"):
             getattr(L, name).restype = ctypes.c_int
         for name in ("od_create", "od_step", "od_dust_state", "od_dust_terms", "od_series", "od_counters",
@@ -432,6 +446,69 @@ class Run:
 
     def set_ions(self, x, v, ids, next_id, a=None):
         od_set_ions(self.h, x, v, ids, next_id, a)
+
+
+class Surrogate:
+    """The learned warm start (od_sur_*): x[B, 8, 7], mask[B, 8], targets[B, 8, 4]."""
+
+    SHAPES = ((256, 16), (256, 256), (256, 512), (256, 256), (16, 256))
+
+    def __init__(self, max_batch=256, seed=0, stream=None):
+        h = ctypes.c_void_p()
+        rc = lib().od_sur_create(int(max_batch), int(seed), stream, ctypes.byref(h))
+        if rc < 0:
+            raise OdError(rc, (lib().od_sur_last_error(None) or b"").decode())
+        self.h = h
+        self.n = lib().od_sur_num_params(h)
+
+    def _chk(self, rc):
+        if rc < 0:
+            raise OdError(rc, (lib().od_sur_last_error(self.h) or b"").decode())
+
+    @staticmethod
+    def _f32(a):
+        return np.ascontiguousarray(a, dtype=np.float32)
+
+    def get_params(self):
+        p = np.zeros(self.n, dtype=np.float32)
+        self._chk(lib().od_sur_get_params(self.h, _ptr(p)))
+        return p
+
+    def set_params(self, p):
+        p = self._f32(p)
+        assert p.size == self.n
+        self._chk(lib().od_sur_set_params(self.h, _ptr(p)))
+
+    def forward(self, x, mask):
+        x, mask = self._f32(x), self._f32(mask)
+        y = np.zeros((x.shape[0], 8, 4), dtype=np.float32)
+        self._chk(lib().od_sur_forward(self.h, _ptr(x), _ptr(mask), x.shape[0], _ptr(y)))
+        return y
+
+    def gradients(self, x, mask, t):
+        x, mask, t = self._f32(x), self._f32(mask), self._f32(t)
+        g = np.zeros(self.n, dtype=np.float32)
+        loss = ctypes.c_double()
+        self._chk(lib().od_sur_gradients(self.h, _ptr(x), _ptr(mask), _ptr(t), x.shape[0], ctypes.byref(loss), _ptr(g)))
+        return loss.value, g
+
+    def train_step(self, x, mask, t, lr):
+        x, mask, t = self._f32(x), self._f32(mask), self._f32(t)
+        loss = ctypes.c_double()
+        self._chk(lib().od_sur_train_step(self.h, _ptr(x), _ptr(mask), _ptr(t), x.shape[0], float(lr),
+                                          ctypes.byref(loss)))
+        return loss.value
+
+    def close(self):
+        if self.h is not None:
+            lib().od_sur_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Batch:
