@@ -58,6 +58,8 @@ extern "C" {
 /* od_params.charge_model (Sec. 2 charging options) */
 #define OD_Q_GIVEN 0      /* constant charges q0 */
 #define OD_Q_CONSISTENT 1 /* OML electron flux + counted absorbed ions */
+#define OD_Q_OML 2        /* constant charges: each grain's isolated-sphere OML floating charge in
+                             the run's flow (q0 ignored), see od_oml_charge */
 
 typedef struct od_dust {
     double x, y, z; /* position, m; the grain must lie inside the cylinder */
@@ -166,6 +168,18 @@ int od_kernel_times(od_handle* h, double* ms, int64_t* launches);
 int od_tune(od_handle* h, int reps, double* ms, int* best_variant, int* best_units_per_block, int* best_blocks_per_sm);
 int od_set_force_config(od_handle* h, int variant, int units_per_block, int blocks_per_sm);
 int od_get_force_config(od_handle* h, int* variant, int* units_per_block, int* blocks_per_sm, int* n_variants);
+
+/* Pipe micro-benchmarks of the current GPU (the ALU roofline of the pair kernel): out[7] =
+ * FP32 FMA / clk / SM, MUFU rsqrt / clk / SM, MUFU ex2 / clk / SM, FP64 FMA / clk / SM,
+ * dependent FP64 FMA latency (clk), dependent FP64 exp latency (clk), the SM clock (MHz)
+ * the per-clock rates are normalised by.  Rates use the nominal clock: rescale by the
+ * clock measured while they ran. */
+int od_measure_peaks(double* out);
+
+/* OML floating charge (C) of an isolated grain of the given radius in the plasma and flow
+ * of p (Sec. 2 "oml" option): the ion current of the drifting Maxwellian with the OML
+ * cross-section balances the Boltzmann electron current.  Host computation. */
+int od_oml_charge(const od_params* p, double radius, double* Q);
 
 /* ---- batches: many independent runs in one launch per step ----
  * The paper's sweeps (Sec. 4: drag versus Mach number, versus collision frequency)

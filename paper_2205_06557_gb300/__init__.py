@@ -36,7 +36,8 @@ F_NO_GRAPH = 64
 
 Q_GIVEN = 0
 Q_CONSISTENT = 1
-_QM = {"given": Q_GIVEN, "consistent": Q_CONSISTENT}
+Q_OML = 2
+_QM = {"given": Q_GIVEN, "consistent": Q_CONSISTENT, "oml": Q_OML}
 
 _d = ctypes.c_double
 
@@ -115,6 +116,8 @@ def lib():
         L.od_batch_last_error.restype = ctypes.c_char_p
         for name in ("od_create_batch", "od_batch_step", "od_batch_size", "od_batch_tune", "od_batch_set_config"):
             getattr(L, name).restype = ctypes.c_int
+        L.od_oml_charge.argtypes = [P(od_params), ctypes.c_double, vp]
+        L.od_oml_charge.restype = ctypes.c_int
         L.od_sur_create.argtypes = [ctypes.c_int, ctypes.c_uint64, vp, P(vp)]
         L.od_sur_destroy.argtypes = [vp]
         L.od_sur_destroy.restype = None
@@ -180,6 +183,14 @@ def make_params(p, stream=None):
     s.eout_grid = int(p.get("eout_grid", 0))
     s.cuda_stream = stream
     return s, keep
+
+
+def od_oml_charge(p, radius):
+    """OML floating charge (C) of a grain of this radius in the plasma and flow of p (host)"""
+    s, keep = make_params(p)
+    q = ctypes.c_double()
+    _check(lib().od_oml_charge(ctypes.byref(s), float(radius), ctypes.byref(q)))
+    return q.value
 
 
 def od_create(p, stream=None):

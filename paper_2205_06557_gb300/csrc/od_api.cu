@@ -86,6 +86,62 @@ void build_vtab(double u, double s, std::vector<double>& tab, double& gmax_b, do
     }
 }
 
+void gl_nodes(int n, std::vector<double>& x, std::vector<double>& w);
+
+// OML currents onto an isolated sphere of radius a at potential phi <= 0 (Sec. 2 "oml"
+// charging): electrons repelled (Boltzmann factor), ions attracted with the orbital
+// cross-section pi a^2 (1 - 2 Z e phi / (m v^2)) from a Maxwellian of thermal speed sig
+// drifting at u.  The ion current is one speed integral of v^3 sigma(v) times the angular
+// average of the shifted Maxwellian, done by Gauss-Legendre on [0, u] and [u, u + 14 sig].
+double oml_ion_current(double a, double phi, double n, double m, double sig, double u, double Z)
+{
+    static std::vector<double> gx, gw;
+    if (gx.empty()) gl_nodes(96, gx, gw);
+    auto integrand = [&](double v) {
+        if (v <= 0.0) return 0.0;
+        const double cross = kPI * a * a * (1.0 - 2.0 * Z * kQE * phi / (m * v * v));
+        double ang;
+        if (u <= 0.0) {
+            ang = 4.0 * kPI * std::exp(-v * v / (2.0 * sig * sig));
+        } else {
+            const double x = v * u / (sig * sig);
+            ang = 2.0 * kPI * (std::exp(-(v - u) * (v - u) / (2 * sig * sig)) - std::exp(-(v + u) * (v + u) / (2 * sig * sig))) / x;
+        }
+        return v * v * v * cross * ang;
+    };
+    const double edges[3] = {0.0, u > 0.0 ? u : 0.0, (u > 0.0 ? u : 0.0) + 14.0 * sig};
+    double total = 0.0;
+    for (int s = 0; s < 2; ++s) {
+        const double lo = edges[s], hi = edges[s + 1];
+        if (!(hi > lo)) continue;
+        for (size_t i = 0; i < gx.size(); ++i) total += 0.5 * (hi - lo) * gw[i] * integrand(0.5 * (lo + hi) + 0.5 * (hi - lo) * gx[i]);
+    }
+    return Z * kQE * n * total * std::pow(2.0 * kPI * sig * sig, -1.5);
+}
+
+// OML floating charge (C): I_ion(phi) = I_electron(phi) by bisection on phi in
+// [-200 k T_e / e, 0], Q = 4 pi eps0 a phi
+double oml_charge(const od_params* p, double a)
+{
+    const double Z = p->ion_charge_number;
+    const double sig = std::sqrt(kKB * p->T_i / p->ion_mass);
+    double u = 0.0;
+    if (p->mach > 0) u = p->mach * std::sqrt(Z * kKB * p->T_e / p->ion_mass);
+    else if (p->E_ext > 0 && p->nu_in > 0) u = Z * kQE * p->E_ext / (p->ion_mass * p->nu_in);
+    const double ne = Z * p->n_inf;
+    auto net = [&](double phi) {
+        const double ie = kQE * ne * kPI * a * a * std::sqrt(8.0 * kKB * p->T_e / (kPI * kME)) * std::exp(kQE * phi / (kKB * p->T_e));
+        return oml_ion_current(a, phi, p->n_inf, p->ion_mass, sig, u, Z) - ie;
+    };
+    double lo = -200.0 * kKB * p->T_e / kQE, hi = 0.0;  // net(lo) > 0 > net(hi)
+    for (int it = 0; it < 200 && hi - lo > 1e-14 * kKB * p->T_e / kQE; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (net(mid) > 0.0) lo = mid;
+        else hi = mid;
+    }
+    return 4.0 * kPI * kEPS0 * a * 0.5 * (lo + hi);
+}
+
 // paper's monomial order of Eq. (Polinomial): alpha_t multiplies r^(2 a_t) z^(2 b_t)
 const int kPowR[15] = {0, 1, 0, 1, 2, 0, 2, 1, 3, 0, 2, 3, 1, 4, 0};
 const int kPowZ[15] = {0, 0, 1, 1, 0, 2, 1, 2, 0, 3, 2, 1, 3, 0, 4};
@@ -274,8 +330,8 @@ int validate(const od_params* p, std::string& msg)
             return OD_EINVAL;
         }
     }
-    if (p->charge_model != OD_Q_GIVEN && p->charge_model != OD_Q_CONSISTENT) {
-        msg = "charge_model must be OD_Q_GIVEN or OD_Q_CONSISTENT";
+    if (p->charge_model != OD_Q_GIVEN && p->charge_model != OD_Q_CONSISTENT && p->charge_model != OD_Q_OML) {
+        msg = "charge_model must be OD_Q_GIVEN, OD_Q_CONSISTENT or OD_Q_OML";
         return OD_EINVAL;
     }
     if (p->n_ions < 0) {
@@ -621,7 +677,8 @@ int create_impl(const od_params* p, od_handle* h)
     Ctrl c0;
     std::memset(&c0, 0, sizeof(c0));
     c0.next_id = (unsigned long long)N;
-    for (int k = 0; k < p->n_dust; ++k) c0.Q[k] = p->dust[k].q0;
+    for (int k = 0; k < p->n_dust; ++k)
+        c0.Q[k] = p->charge_model == OD_Q_OML ? oml_charge(p, p->dust[k].radius) : p->dust[k].q0;
     OD_CK(h, cudaMemcpyAsync(B.ctrl, &c0, sizeof(Ctrl), cudaMemcpyHostToDevice, h->stream));
     int rc = replan(h, N);
     if (rc) return rc;
@@ -911,6 +968,18 @@ int od_kernel_times(od_handle* h, double* ms, int64_t* launches)
 }
 
 const char* od_last_error(const od_handle* h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+int od_oml_charge(const od_params* p, double radius, double* Q)
+{
+    std::string msg;
+    if (!Q || !(radius > 0) || !std::isfinite(radius)) return fail(nullptr, OD_EINVAL, "bad radius or output");
+    od_params q = *p;
+    q.n_dust = 0;
+    const int rc = validate(&q, msg);
+    if (rc) return fail(nullptr, rc, msg);
+    *Q = oml_charge(p, radius);
+    return OD_OK;
+}
 
 static const int kTuneGrains[4] = {4, 8, 16, 32};
 static const int kTuneBps[3] = {0, 4, 2};  // persistent CTAs per SM: 0 = occupancy limit

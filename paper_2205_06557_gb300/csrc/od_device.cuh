@@ -91,13 +91,20 @@ __device__ double invert_flux(double target, double lo, double hi, double v, dou
         if (g < 0) lo = v;
         else hi = v;
         const double dg = fabs(v) * npdf((v - u) / s) / s;
+        // converged once the Newton correction is below ~1e-13 of the speed scale; the
+        // check comes before the bracket test, which a sub-ulp step would fail
+        const double tol = 1e-13 * fmax(fabs(v), s);
+        if (dg > 0) {
+            const double step = g / dg;
+            if (fabs(step) <= tol) {
+                v -= step;
+                break;
+            }
+        }
         double vn = dg > 0 ? v - g / dg : 0.5 * (lo + hi);
         if (!(vn > lo && vn < hi)) vn = 0.5 * (lo + hi);
-        // converged to ~1e-13 of the speed scale (a few hundred ulp above FP64 rounding)
-        const double tol = 1e-13 * fmax(fabs(vn), s);
-        const bool done = fabs(vn - v) <= tol || hi - lo <= tol;
         v = vn;
-        if (done) break;
+        if (hi - lo <= tol) break;
     }
     return v;
 }

@@ -53,6 +53,17 @@ def test_invalid_parameters_rejected_on_host(L, change):
     assert rc == -1 and msg
 
 
+@pytest.mark.parametrize("mach,nu,a", [(1.0, 1e6, 2e-5), (0.3, 0.0, 8e-6), (2.0, 5e6, 1.5e-5), (1e-9, 0.0, 1e-5)])
+def test_library_oml_charge_matches_oracle(L, mach, nu, a):
+    """host-side OML charge of the library (Gauss-Legendre) vs the oracle's (scipy quad)"""
+    from oracle import oml
+
+    p = dict(W.tiny(), mach=mach, nu=nu)
+    q_lib = od.od_oml_charge(p, a)
+    q_ref = oml.oml_charge(a, p["n_inf"], p["m_i"], p["T_i"], p["T_e"], mach)
+    assert abs(q_lib / q_ref - 1) < 1e-9
+
+
 def test_null_arguments(L):
     assert L.od_create(None, None) == -1
     assert L.od_step(None, 1) == -1
