@@ -1,0 +1,59 @@
+"""Warm-start pipeline: host-side pieces on CPU (features, targets, convergence
+criterion), and a small end-to-end run on the GPU showing what the trained network
+gains over starting the consistent charge iteration from zero."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2205_06557_gb300 import build
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    build.build()
+
+
+def test_features_and_targets_are_consistent():
+    from paper_2205_06557_gb300 import warmstart as ws
+
+    p = ws.study_run(3, 1000)
+    x, m = ws.features(p)
+    D = len(p["dust"])
+    assert 1 <= D <= 4 and m.sum() == D and np.all(m[D:] == 0)
+    assert np.all(np.abs(x[:D, 3:6]) <= 1.0) and np.all(np.abs(x[:D, 6]) <= 1.0)
+    # q0 is the OML charge, so its potential offset target is zero
+    q = np.array([g["q0"] for g in p["dust"]])
+    t = ws.targets(p, q, np.zeros((D, 3)))
+    assert np.allclose(t[:D, 0], 0.0, atol=1e-6)
+    # the network's charge map inverts the target map
+    assert all(g["q0"] < 0 for g in p["dust"])
+
+
+def test_steps_to_converge():
+    from paper_2205_06557_gb300.warmstart import steps_to_converge
+
+    t = np.arange(1000)
+    q = -1e5 * (1 - np.exp(-t / 100.0))
+    # |q - q_ref| <= 1% |q_ref| from exp(-t/100) <= 0.01, i.e. t >= 461
+    assert steps_to_converge(q, -1e5, 0.01) == math.ceil(100 * math.log(100))
+    assert steps_to_converge(np.full(10, -1e5), -1e5, 0.01) == 0
+
+
+@pytest.mark.gpu
+def test_warm_start_pipeline_beats_zero_start():
+    from paper_2205_06557_gb300 import warmstart as ws
+
+    # a dense plasma (charging time ~2,400 steps) in a small domain (~6,000 ions) keeps
+    # the label and evaluation runs short enough to converge in a test
+    dom = dict(n_inf=1e15, R=1e-4, H=2e-4)
+    plist, X, M, T = ws.generate(48, 10000, seed0=0, batch_runs=48, **dom)
+    assert X.shape == (48, 8, 7) and np.isfinite(T).all()
+    net, norm, losses, vlosses = ws.train(X, M, T, iters=400, batch=32)
+    assert losses[-30:].mean() < losses[:30].mean()
+    evalp = [ws.study_run(10_000 + s, 8000, **dom) for s in range(6)]
+    steps, err0 = ws.evaluate(net, norm, evalp, 8000, tol=0.02)
+    # starting from zero charge is far from converged; the network starts close
+    assert np.median(err0["net"]) < 0.2 * np.median(err0["zero"])
+    assert steps["net"].mean() < steps["zero"].mean()
+    net.close()
