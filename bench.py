@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--pair-config", default="tuned",
+                    help="pair-kernel choice 'variant,units_per_block,ctas_per_sm' instead of the autotuner's")
     return ap.parse_args()
 
 
@@ -185,8 +187,12 @@ def run_ours(args):
     run = od.Run(p, stream=ctypes_stream(stream))
     N = run.N
     info = run.info()
-    # pair-kernel autotuner (untimed; cached per device and ion count)
-    tv, tg, tb, _ = od.tune_cached(run.h, "%s|N=%d" % (torch.cuda.get_device_name(local), N))
+    if args.pair_config == "tuned":
+        # pair-kernel autotuner (untimed; cached per device and ion count)
+        tv, tg, tb, _ = od.tune_cached(run.h, "%s|N=%d" % (torch.cuda.get_device_name(local), N))
+    else:
+        tv, tg, tb = (int(t) for t in args.pair_config.split(","))
+        od.od_set_force_config(run.h, tv, tg, tb)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
 
     for _ in range(args.warmup):

@@ -438,6 +438,12 @@ __device__ __forceinline__ void pair_chunk(const float4* __restrict__ fpos, int 
         __syncthreads();
         sj[threadIdx.x] = fpos[jb + threadIdx.x];
         __syncthreads();
+        // blocked summation: each shared tile of BT sources is summed on its own and
+        // then added to the running sum, so the FP32 rounding error grows like
+        // sqrt(BT) + sqrt(n / BT) instead of sqrt(n) over n same-sign terms
+        float bx[IPT], by[IPT], bz[IPT];
+#pragma unroll
+        for (int k = 0; k < IPT; ++k) bx[k] = by[k] = bz[k] = 0.f;
 #pragma unroll 8
         for (int jj = 0; jj < BT; ++jj) {
             const float4 pj = sj[jj];
@@ -452,10 +458,16 @@ __device__ __forceinline__ void pair_chunk(const float4* __restrict__ fpos, int 
                 const float e = ex2_approx(-s);
                 const float f = fmaf(s, LN2, 1.0f);
                 const float c3 = (f * e) * (ri * ri * ri);
-                ax[k] = fmaf(c3, dx, ax[k]);
-                ay[k] = fmaf(c3, dy, ay[k]);
-                az[k] = fmaf(c3, dz, az[k]);
+                bx[k] = fmaf(c3, dx, bx[k]);
+                by[k] = fmaf(c3, dy, by[k]);
+                bz[k] = fmaf(c3, dz, bz[k]);
             }
+        }
+#pragma unroll
+        for (int k = 0; k < IPT; ++k) {
+            ax[k] += bx[k];
+            ay[k] += by[k];
+            az[k] += bz[k];
         }
     }
 }
