@@ -32,6 +32,10 @@ from paper_2205_06557_gb300 import workloads as W  # noqa: E402
 METRIC = "ion pair-interactions/s"
 UNIT = "pairs/s"
 PAIRS_PER_CLK_SM = 8.0  # FP32 pipe (16 FP32 ops / pair at 128 lanes) and SFU (2 MUFU / pair at 16 lanes)
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch, from the full ncu capture of
+# that kernel on that ion count (profiles/k_forces_at_scale_200k.md); any other kernel or
+# size reports null until it has been captured
+NCU_DRAM_BYTES = {("k_forces<256,2>", 199969): 3217152}
 
 
 def parse():
@@ -258,6 +262,7 @@ def run_ours(args):
     clk_max = float(pk.get("sm_max_mhz") or clk.get("sm_max_mhz") or 2070.0)
     peak = sms * clk_max * 1e6 * PAIRS_PER_CLK_SM
     k1_ms = kms[1] / max(kn[1], 1)
+    kname = "k_forces<%d,%d>" % od.force_variant_shape(tv)
     k1_rate = float(N) * (N - 1) / (k1_ms / 1e3)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -273,8 +278,8 @@ def run_ours(args):
         "wall_s_timed": wall,
         "kernel_ms_per_step": {"push_scan_inject": kms[0] / max(kn[0], 1), "pair_forces": k1_ms,
                                "kick_collide": kms[2] / max(kn[2], 1), "grain_update": kms[3] / max(kn[3], 1)},
-        "roofline": {"bound": "alu", "kernel": "k_forces", "achieved": k1_rate / 1e9, "peak": peak / 1e9,
-                     "unit": "Gpair/s", "frac": k1_rate / peak, "traffic": None,
+        "roofline": {"bound": "alu", "kernel": kname, "achieved": k1_rate / 1e9, "peak": peak / 1e9,
+                     "unit": "Gpair/s", "frac": k1_rate / peak, "traffic": NCU_DRAM_BYTES.get((kname, N)),
                      "peak_basis": "%d SMs x %.0f MHz x %.0f pairs/clk/SM (FP32 pipe and SFU limits)"
                                    % (sms, clk_max, PAIRS_PER_CLK_SM)},
         "clocks": clk,
