@@ -31,7 +31,12 @@ from paper_2205_06557_gb300 import workloads as W  # noqa: E402
 
 METRIC = "ion pair-interactions/s"
 UNIT = "pairs/s"
-PAIRS_PER_CLK_SM = 8.0  # FP32 pipe (16 FP32 ops / pair at 128 lanes) and SFU (2 MUFU / pair at 16 lanes)
+# ALU roofline of the pair kernels, in ordered pairs per clock per SM: min(128 FP32 lanes /
+# FP32 ops per ordered pair, 16 MUFU lanes / MUFU ops per ordered pair).  The ordered-pair
+# kernel spends 14 FP32 ops and 2 MUFU (rsqrt, ex2) on each ordered pair; the symmetric one
+# 17 FP32 ops (3 more for the source's sum) and 2 MUFU on each unordered pair, applied to
+# both ions, i.e. 8.5 FP32 and 1 MUFU per ordered pair.
+PAIRS_PER_CLK_SM = {0: min(128 / 14, 16 / 2), 1: min(128 / 8.5, 16 / 1)}
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch, from the full ncu capture of
 # that kernel on that ion count (profiles/k_forces_at_scale_200k.md); any other kernel or
 # size reports null until it has been captured
@@ -260,9 +265,10 @@ def run_ours(args):
     pk = peaks()
     sms = int(info["sms"])
     clk_max = float(pk.get("sm_max_mhz") or clk.get("sm_max_mhz") or 2070.0)
-    peak = sms * clk_max * 1e6 * PAIRS_PER_CLK_SM
+    sym = od.FORCE_VARIANTS[tv][2]
+    peak = sms * clk_max * 1e6 * PAIRS_PER_CLK_SM[sym]
     k1_ms = kms[1] / max(kn[1], 1)
-    kname = "k_forces<%d,%d>" % od.force_variant_shape(tv)
+    kname = od.force_variant_name(tv)
     k1_rate = float(N) * (N - 1) / (k1_ms / 1e3)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -271,7 +277,7 @@ def run_ours(args):
         "config": {"workload": desc, "n_ions": N, "n_dust": run.D, "steps_timed": args.steps,
                    "l2": "flushed between timed steps (256 MB write)", "parallelism": "replicas" if world > 1 else "1 GPU",
                    "precision": "pair forces FP32; ion state, grain sums and averages FP64",
-                   "pair_kernel": {"threads": od.force_variant_shape(tv)[0], "targets_per_thread":
+                   "pair_kernel": {"kernel": kname, "threads": od.force_variant_shape(tv)[0], "targets_per_thread":
                                    od.force_variant_shape(tv)[1], "units_per_block": tg,
                                    "ctas_per_sm": tb or "occupancy limit"}},
         "ion_steps_per_s": world * float(N) * args.steps / (t_max / 1e3),
@@ -280,8 +286,9 @@ def run_ours(args):
                                "kick_collide": kms[2] / max(kn[2], 1), "grain_update": kms[3] / max(kn[3], 1)},
         "roofline": {"bound": "alu", "kernel": kname, "achieved": k1_rate / 1e9, "peak": peak / 1e9,
                      "unit": "Gpair/s", "frac": k1_rate / peak, "traffic": NCU_DRAM_BYTES.get((kname, N)),
-                     "peak_basis": "%d SMs x %.0f MHz x %.0f pairs/clk/SM (FP32 pipe and SFU limits)"
-                                   % (sms, clk_max, PAIRS_PER_CLK_SM)},
+                     "peak_basis": "%d SMs x %.0f MHz x %.2f ordered pairs/clk/SM (FP32 pipe and SFU limits of %s)"
+                                   % (sms, clk_max, PAIRS_PER_CLK_SM[sym],
+                                      "17 FP32 + 2 MUFU per unordered pair" if sym else "14 FP32 + 2 MUFU per pair")},
         "clocks": clk,
         "gpu_launches": 4 * args.steps * world,
         "e2e": {"value": e2e_units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

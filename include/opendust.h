@@ -157,11 +157,18 @@ int od_set_profiling(od_handle* h, int on);
 int od_kernel_times(od_handle* h, double* ms, int64_t* launches);
 
 /* Pair-kernel autotuner (the all-pairs force evaluation of Sec. 5 is the hot spot).
- * od_tune times every kernel variant (threads per block x targets per thread) at four
- * work granularities (4, 8, 16, 32 units per persistent block) and three persistent
- * grid sizes (CTAs per SM: the occupancy limit, 4, 2) on the run's current ions, reps
- * launches each, keeps the fastest and writes the average ms per launch to
- * ms[n_variants][4][3] (host, may be NULL; -1 where a cap is not below the limit).
+ * Variants 0-7 evaluate every ordered pair (threads per block x targets per thread:
+ * 64x1, 64x2, 128x2, 128x4, 256x2, 256x4, 128x8, 64x8); variants 8-11 evaluate each
+ * unordered pair once and apply it to both ions (Newton's third law; 128x2, 128x4,
+ * 256x2, 256x4), at the price of one partial-sum slot per tile of BT x IPT ions for
+ * every ion (device memory N_pad^2 / (BT IPT) x 16 bytes, allocated by the call that
+ * selects the variant).  Both kinds give forces within FP32 rounding of each other.
+ * od_tune times every variant at four work granularities (4, 8, 16, 32 units per
+ * persistent block; the symmetric variants have fixed-size units and are timed at the
+ * first only) and three persistent grid sizes (CTAs per SM: the occupancy limit, 4, 2)
+ * on the run's current ions, reps launches each, keeps the fastest and writes the
+ * average ms per launch to ms[n_variants][4][3] (host, may be NULL; -1 where a setting
+ * is not timed).
  * od_set_force_config applies a known choice (e.g. from a cache; blocks_per_sm 0 =
  * occupancy limit) and od_get_force_config reports the current one and the number of
  * variants.  The ion state is not changed; call between steps. */

@@ -295,12 +295,20 @@ def od_selftest_wait_timeout(h, polls=2000):
     return lib().od_selftest_wait_timeout(h, int(polls))
 
 
-FORCE_VARIANTS = ((64, 1), (64, 2), (128, 2), (128, 4), (256, 2), (256, 4), (128, 8), (64, 8))
+# (threads per block, targets per thread, symmetric) of each pair-kernel variant: the
+# ordered-pair kernel k_forces, then the symmetric (Newton III) kernel k_forces_sym
+FORCE_VARIANTS = ((64, 1, 0), (64, 2, 0), (128, 2, 0), (128, 4, 0), (256, 2, 0), (256, 4, 0), (128, 8, 0),
+                  (64, 8, 0), (128, 2, 1), (128, 4, 1), (256, 2, 1), (256, 4, 1))
 
 
 def force_variant_shape(v):
     """(threads per block, targets per thread) of pair-kernel variant v"""
-    return FORCE_VARIANTS[v]
+    return FORCE_VARIANTS[v][:2]
+
+
+def force_variant_name(v):
+    bt, ipt, sym = FORCE_VARIANTS[v]
+    return "k_forces%s<%d,%d>" % ("_sym" if sym else "", bt, ipt)
 
 
 def od_get_force_config(h):

@@ -488,6 +488,16 @@ ForceArgs plan_forces(int N, int v, int sms, int units_per_block, int bps_cap)
     const int n_it = F.n_pad / F.TI;
     const int occ = force_blocks_per_sm(v);
     const long long gmax = (long long)sms * (bps_cap > 0 ? std::min(bps_cap, occ) : occ);
+    if (fv.sym) {
+        // tile pairs (I, J >= I); units have a fixed size, so units_per_block is unused
+        F.sym = 1;
+        F.JC = F.TI;
+        F.JS = n_it;
+        F.W = n_it;
+        F.U = (long long)n_it * (n_it + 1) / 2;
+        F.G = (int)std::min<long long>(gmax, F.U);
+        return F;
+    }
     long long js = (units_per_block * gmax + n_it - 1) / n_it;
     js = std::max(1ll, std::min(js, (long long)F.n_pad / fv.BT));
     long long jc = ((F.n_pad + js - 1) / js + fv.BT - 1) / fv.BT * fv.BT;
@@ -505,10 +515,17 @@ ForceArgs plan_forces(int N, int v, int sms, int units_per_block, int bps_cap)
     return F;
 }
 
+// untuned choice: ordered pairs for small runs (many small units spread over the SMs),
+// the symmetric kernel (half the pair evaluations) above 32k ions while its partial slots
+// (N_pad^2 / tile x 16 bytes) stay within 4 GB (512-ion tiles) or 16 GB (1024-ion tiles)
 int default_variant(int N)
 {
     if (N <= 4096) return 0;
     if (N <= 32768) return 2;
+    const int sym512 = 9, sym1024 = 11;  // k_forces_sym<128,4>, k_forces_sym<256,4>
+    const double n = (double)N + 1024.0;
+    if (n * n / 512.0 * 16.0 <= 4.0 * (1ull << 30)) return sym512;
+    if (n * n / 1024.0 * 16.0 <= 16.0 * (1ull << 30)) return sym1024;
     return 3;
 }
 
@@ -656,7 +673,9 @@ int create_impl(const od_params* p, od_handle* h)
     h->cap = std::max(N, 1);
     h->npad_cap = ((long long)h->cap + 1023) / 1024 * 1024;
     h->nb_cap = (h->cap + kick_block() - 1) / kick_block();
-    h->variant = -1;
+    // untuned runs start from the size-based default; batch members are re-planned by
+    // their batch (ordered-pair units) and need no symmetric partial slots meanwhile
+    h->variant = h->batch_member ? 3 : -1;
     Bufs& B = h->B;
     B.cap = h->cap;
     for (int b = 0; b < 2; ++b) {
@@ -918,9 +937,7 @@ int od_set_ions(od_handle* h, const double* x, const double* v, const double* a,
     unsigned long long nid = next_id;
     OD_CK(h, cudaMemcpyAsync((char*)h->B.ctrl + offsetof(Ctrl, next_id), &nid, sizeof(nid), cudaMemcpyHostToDevice,
                              h->stream));
-    const int variant = h->variant;
     if ((rc = replan(h, (int)n))) return rc;
-    (void)variant;
     h->graph_ok = false;
     OD_LK(h, launch_fpos(h->P, h->B, buf, h->stream));
     if (a) {
@@ -1023,15 +1040,31 @@ int od_tune(od_handle* h, int reps, double* ms, int* best_variant, int* best_upb
     }
     double best = 1e300;
     int bv = h->variant, bg = h->upb, bb = h->bps;
+    size_t free_b = 0, total_b = 0;
+    OD_CK(h, cudaMemGetInfo(&free_b, &total_b));
+    const double slot_budget = (double)(free_b + sizeof(float4) * (size_t)h->part_cap) / 8.0;
     for (int v = 0; v < nv; ++v)
         for (int g = 0; g < 4; ++g)
             for (int c = 0; c < 3; ++c) {
                 if (kTuneBps[c] >= force_blocks_per_sm(v)) continue;  // no cap below the occupancy limit
+                const ForceVariant fv = force_variant(v);
+                if (fv.sym) {
+                    if (g > 0) continue;  // fixed-size units: one grain setting
+                    // one partial slot per tile for every ion: skip layouts that would take
+                    // more than an eighth of the device memory
+                    const double ti = fv.BT * fv.IPT, np = std::ceil(h->P.N / ti) * ti;
+                    if (np / ti * np * sizeof(float4) > slot_budget) continue;
+                }
                 int rc = apply_force_config(h, v, kTuneGrains[g], kTuneBps[c]);
                 if (rc) return rc;
+                // the kick is timed too: it sums every ion's partial slots, one per tile
+                // for the symmetric kernel
                 OD_LK(h, launch_forces(h->P, h->B, h->F, h->variant, h->stream));
                 OD_CK(h, cudaEventRecord(h->ev[0], h->stream));
-                for (int r = 0; r < reps; ++r) OD_LK(h, launch_forces(h->P, h->B, h->F, h->variant, h->stream));
+                for (int r = 0; r < reps; ++r) {
+                    OD_LK(h, launch_forces(h->P, h->B, h->F, h->variant, h->stream));
+                    OD_LK(h, launch_kick(h->P, h->B, h->F, 1, h->stream));
+                }
                 OD_CK(h, cudaEventRecord(h->ev[1], h->stream));
                 OD_CK(h, cudaEventSynchronize(h->ev[1]));
                 float t = 0.f;
@@ -1047,9 +1080,17 @@ int od_tune(od_handle* h, int reps, double* ms, int* best_variant, int* best_upb
             }
     int rc = apply_force_config(h, bv, bg, bb);
     if (rc) return rc;
-    // the last force evaluation's partial sums belong to the configuration just left:
-    // recompute them for the chosen one so the next kick reads a consistent layout
-    OD_LK(h, launch_forces(h->P, h->B, h->F, h->variant, h->stream));
+    // give back partial-slot memory beyond what the chosen layout needs
+    if (h->part_cap > 2 * (long long)h->F.W * h->F.n_pad) {
+        OD_CK(h, cudaStreamSynchronize(h->stream));
+        cudaFree(h->B.part);
+        h->B.part = nullptr;
+        h->part_cap = 0;
+        if ((rc = ensure_part(h))) return rc;
+    }
+    // the accelerations and partial sums left by the timing belong to other kernels:
+    // evaluate the current state again with the chosen one
+    if ((rc = force_eval(h))) return rc;
     OD_CK(h, cudaStreamSynchronize(h->stream));
     if (best_variant) *best_variant = bv;
     if (best_upb) *best_upb = bg;
@@ -1246,6 +1287,7 @@ int od_create_batch(const od_params* ps, int32_t R, od_batch** out)
         od_params p = ps[r];
         p.cuda_stream = b->stream;
         od_handle* h = new od_handle();
+        h->batch_member = true;
         rc = create_impl(&p, h);
         if (rc) {
             b->err = "run " + std::to_string(r) + ": " + h->err;

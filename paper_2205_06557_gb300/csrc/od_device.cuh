@@ -422,18 +422,31 @@ __device__ __forceinline__ int owner_of(long long u, long long U, int G)
     return (int)(((u + 1) * (long long)G - 1) / U);
 }
 
+// Pair coefficient in scaled coordinates s = r log2(e) / lambda_De, which make
+// exp(-r/lambda) = 2^-s and 1 + r/lambda = 1 + s ln 2.  For d = s_j - s_i and
+// r2 = |d|^2 + eps (eps keeps a self pair finite: its d is exactly 0) the term of Eq. 1's
+// ion-ion part is d (1 + s ln2) 2^-s / s^3.  With ri = 1/s, (1 + s ln2) ri^3 =
+// ri^2 (ri + ln2) since s ri = 1 (up to the rsqrt rounding, 2e-7 relative), one product
+// fewer than the literal form.
+__device__ __forceinline__ float pair_c3(float dx, float dy, float dz)
+{
+    constexpr float EPS2 = 1e-24f;
+    constexpr float LN2 = 0.69314718055994531f;
+    float r2 = fmaf(dx, dx, EPS2);
+    r2 = fmaf(dy, dy, r2);
+    r2 = fmaf(dz, dz, r2);
+    const float ri = rsqrt_approx(r2);
+    const float e = ex2_approx(-(r2 * ri));
+    return (e * (ri * ri)) * (ri + LN2);
+}
+
 // Accumulate into IPT targets per thread the pair terms of sources [j0, j1), staged
-// through shared memory BT at a time.  Scaled coordinates s = r log2(e) / lambda_De
-// make exp(-r/lambda) = 2^-s and 1 + r/lambda = 1 + s ln 2.  Per pair: d = s_j - s_i,
-// r2 = |d|^2 + eps (eps keeps the self pair finite: its d is exactly 0),
-// acc += d (1 + s ln2) 2^-s / s^3.
+// through shared memory BT at a time (acc += d c3, c3 from pair_c3).
 template <int BT, int IPT>
 __device__ __forceinline__ void pair_chunk(const float4* __restrict__ fpos, int j0, int j1, const float* xi,
                                            const float* yi, const float* zi, float* ax, float* ay, float* az,
                                            float4* sj)
 {
-    constexpr float EPS2 = 1e-24f;
-    constexpr float LN2 = 0.69314718055994531f;
     for (int jb = j0; jb < j1; jb += BT) {
         __syncthreads();
         sj[threadIdx.x] = fpos[jb + threadIdx.x];
@@ -450,14 +463,7 @@ __device__ __forceinline__ void pair_chunk(const float4* __restrict__ fpos, int 
 #pragma unroll
             for (int k = 0; k < IPT; ++k) {
                 const float dx = pj.x - xi[k], dy = pj.y - yi[k], dz = pj.z - zi[k];
-                float r2 = fmaf(dx, dx, EPS2);
-                r2 = fmaf(dy, dy, r2);
-                r2 = fmaf(dz, dz, r2);
-                const float ri = rsqrt_approx(r2);
-                const float s = r2 * ri;
-                const float e = ex2_approx(-s);
-                const float f = fmaf(s, LN2, 1.0f);
-                const float c3 = (f * e) * (ri * ri * ri);
+                const float c3 = pair_c3(dx, dy, dz);
                 bx[k] = fmaf(c3, dx, bx[k]);
                 by[k] = fmaf(c3, dy, by[k]);
                 bz[k] = fmaf(c3, dz, bz[k]);
@@ -506,6 +512,121 @@ __global__ void __launch_bounds__(BT) k_forces(const float4* __restrict__ fpos, 
         float4* out = part + (long long)slot * F.n_pad + t * F.TI + threadIdx.x;
 #pragma unroll
         for (int k = 0; k < IPT; ++k) out[k * BT] = make_float4(ax[k], ay[k], az[k], 0.f);
+    }
+}
+
+// Unit u of the row-major upper triangle of T x T tiles (J >= I), where row I starts
+// at I T - I (I - 1) / 2.
+__device__ __forceinline__ void tri_unit(long long u, int T, int& I, int& J)
+{
+    const double b = 2.0 * T + 1.0;
+    long long i = (long long)((b - sqrt(fmax(b * b - 8.0 * (double)u, 0.0))) * 0.5);
+    i = max(0ll, min(i, (long long)T - 1));
+    while (i > 0 && i * T - i * (i - 1) / 2 > u) --i;
+    while (i + 1 < T && (i + 1) * T - (i + 1) * i / 2 <= u) ++i;
+    I = (int)i;
+    J = (int)(I + (u - (i * T - i * (i - 1) / 2)));
+}
+
+// Symmetric (Newton III) all-pairs kernel: each unordered pair is evaluated once and
+// applied to both ions.  Tiles of TI = BT IPT ions; units are the tile pairs (I, J >= I)
+// in row-major order, split into contiguous ranges over the persistent blocks.
+//
+// Unit (I, J > I): warp w holds 32 IPT targets of tile I (IPT per lane) and walks tile J
+// in groups of 32 sources, one per lane.  Each source travels round the warp by shuffles
+// together with its own accumulator, so after 32 rotations every lane has met every
+// source of the group and each accumulator is back on its lane.  The source-side sums of
+// the warps are combined in shared memory in a fixed warp order, SUB sources at a time
+// (double buffered, one barrier per SUB sources).
+// Unit (I, I): the ordered pairs of the tile through pair_chunk (the self pair is 0).
+//
+// Partial slots (deterministic, each written exactly once per evaluation): the target-
+// side sum of unit (I, J) goes to slot J of the ions of tile I, its source-side sum to
+// slot I of the ions of tile J, and unit (I, I) fills slot I of tile I.  Every ion has
+// T slots, summed by the kick.
+template <int BT, int IPT>
+__global__ void __launch_bounds__(BT) k_forces_sym(const float4* __restrict__ fpos, float4* __restrict__ part,
+                                                   ForceArgs F)
+{
+    constexpr int NW = BT / 32;
+    constexpr int TI = BT * IPT;
+    constexpr int SUB = 128;
+    static_assert(TI % SUB == 0 && (TI / SUB) % 2 == 0, "tile must hold an even number of combine steps");
+    __shared__ float s_acc[2][3][NW][SUB];
+    __shared__ float4 sj[BT];
+    const int T = F.JS;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int src = (lane + 1) & 31;
+    long long u = (long long)blockIdx.x * F.U / F.G;
+    const long long u_end = (long long)(blockIdx.x + 1) * F.U / F.G;
+    if (u >= u_end) return;
+    int I, J;
+    tri_unit(u, T, I, J);
+    for (; u < u_end; ++u) {
+        float xi[IPT], yi[IPT], zi[IPT], ax[IPT], ay[IPT], az[IPT];
+#pragma unroll
+        for (int k = 0; k < IPT; ++k) {
+            const float4 p = fpos[I * TI + k * BT + threadIdx.x];
+            xi[k] = p.x;
+            yi[k] = p.y;
+            zi[k] = p.z;
+            ax[k] = 0.f;
+            ay[k] = 0.f;
+            az[k] = 0.f;
+        }
+        if (I == J) {
+            pair_chunk<BT, IPT>(fpos, I * TI, I * TI + TI, xi, yi, zi, ax, ay, az, sj);
+        } else {
+            const int jb = J * TI;
+            for (int sc = 0; sc < TI / SUB; ++sc) {
+                const int buf = sc & 1;
+#pragma unroll 1
+                for (int q = 0; q < SUB / 32; ++q) {
+                    const float4 pj = __ldg(fpos + jb + sc * SUB + q * 32 + lane);
+                    float xj = pj.x, yj = pj.y, zj = pj.z, bx = 0.f, by = 0.f, bz = 0.f;
+#pragma unroll 4
+                    for (int r = 0; r < 32; ++r) {
+#pragma unroll
+                        for (int k = 0; k < IPT; ++k) {
+                            const float dx = xj - xi[k], dy = yj - yi[k], dz = zj - zi[k];
+                            const float c3 = pair_c3(dx, dy, dz);
+                            ax[k] = fmaf(c3, dx, ax[k]);
+                            ay[k] = fmaf(c3, dy, ay[k]);
+                            az[k] = fmaf(c3, dz, az[k]);
+                            bx = fmaf(-c3, dx, bx);
+                            by = fmaf(-c3, dy, by);
+                            bz = fmaf(-c3, dz, bz);
+                        }
+                        xj = __shfl_sync(0xffffffffu, xj, src);
+                        yj = __shfl_sync(0xffffffffu, yj, src);
+                        zj = __shfl_sync(0xffffffffu, zj, src);
+                        bx = __shfl_sync(0xffffffffu, bx, src);
+                        by = __shfl_sync(0xffffffffu, by, src);
+                        bz = __shfl_sync(0xffffffffu, bz, src);
+                    }
+                    s_acc[buf][0][w][q * 32 + lane] = bx;
+                    s_acc[buf][1][w][q * 32 + lane] = by;
+                    s_acc[buf][2][w][q * 32 + lane] = bz;
+                }
+                // the other buffer's readers (previous combine step) finished before they
+                // reached this barrier, so the next step may refill it without another one
+                __syncthreads();
+                for (int j = threadIdx.x; j < SUB; j += BT) {
+                    float sx = 0.f, sy = 0.f, sz = 0.f;
+#pragma unroll
+                    for (int ww = 0; ww < NW; ++ww) {
+                        sx += s_acc[buf][0][ww][j];
+                        sy += s_acc[buf][1][ww][j];
+                        sz += s_acc[buf][2][ww][j];
+                    }
+                    part[(long long)I * F.n_pad + jb + sc * SUB + j] = make_float4(sx, sy, sz, 0.f);
+                }
+            }
+        }
+        float4* out = part + (long long)J * F.n_pad + I * TI + threadIdx.x;
+#pragma unroll
+        for (int k = 0; k < IPT; ++k) out[k * BT] = make_float4(ax[k], ay[k], az[k], 0.f);
+        if (++J == T) J = ++I;
     }
 }
 
@@ -567,15 +688,28 @@ __device__ __forceinline__ void kick_body(const Phys& P, const Bufs& B, const Fo
         z = X[2 * cap + i];
         float ax = 0.f, ay = 0.f, az = 0.f;
         if (!(P.flags & OD_F_NO_IONION)) {
-            const int t = i / F.TI;
-            const long long u0 = (long long)t * F.JS;
-            const int g0 = owner_of(u0, F.U, F.G), g1 = owner_of(u0 + F.JS - 1, F.U, F.G);
+            // slots of this ion: the blocks that covered its tile (ordered-pair kernel) or
+            // one per tile (symmetric kernel)
+            int ns = F.W;
+            if (!F.sym) {
+                const int t = i / F.TI;
+                const long long u0 = (long long)t * F.JS;
+                ns = owner_of(u0 + F.JS - 1, F.U, F.G) - owner_of(u0, F.U, F.G) + 1;
+            }
+            // blocked sum over the slots (up to ~1000 with the symmetric kernel)
+            for (int s0 = 0; s0 < ns; s0 += 16) {
+                const int s1 = min(ns, s0 + 16);
+                float bx = 0.f, by = 0.f, bz = 0.f;
 #pragma unroll 8
-            for (int s = 0; s <= g1 - g0; ++s) {
-                const float4 p = __ldcs(B.part + (long long)s * F.n_pad + i);
-                ax += p.x;
-                ay += p.y;
-                az += p.z;
+                for (int s = s0; s < s1; ++s) {
+                    const float4 p = __ldcs(B.part + (long long)s * F.n_pad + i);
+                    bx += p.x;
+                    by += p.y;
+                    bz += p.z;
+                }
+                ax += bx;
+                ay += by;
+                az += bz;
             }
             ax *= -P.k_ii;
             ay *= -P.k_ii;

@@ -116,7 +116,8 @@ struct ForceArgs {
     int JS;      // chunks per tile
     int G;       // persistent blocks
     int W;       // partial slots
-    long long U; // units = n_itiles * JS
+    long long U; // units = n_itiles * JS (symmetric: T (T + 1) / 2 tile pairs)
+    int sym;     // 1: symmetric kernel, JC = TI, JS = W = T tiles, every ion has T slots
 };
 
 // One run of a batched launch (od_batch.cu): its parameters, buffers and pair plan.
@@ -155,9 +156,9 @@ int launch_stats(const Phys& P, const Bufs& B, double* mean_se, cudaStream_t s);
 int launch_eout_grid(double R, double H, double lam, int nx, int nz, int nq, const double* gl_x,
                      const double* gl_w, double* out, cudaStream_t s);
 
-// pair-kernel variants: (threads per block, targets per thread)
+// pair-kernel variants: (threads per block, targets per thread, symmetric)
 struct ForceVariant {
-    int BT, IPT;
+    int BT, IPT, sym;
 };
 int num_force_variants();
 ForceVariant force_variant(int v);

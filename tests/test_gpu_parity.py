@@ -75,7 +75,7 @@ GRAINS = [(0.0, 0.0, -6e-5, 1.0e-5, -1500.0), (4e-5, 0.0, 7e-5, 1.2e-5, 800.0), 
           (-1e-4, 1e-5, -0.5e-4, 0.6e-5, -700.0)]
 
 
-def _force_case(n, n_dust, flags=0):
+def _force_case(n, n_dust, flags=0, variant=None):
     p = W.tiny()
     p.update(n_ions=max(n, 1), charge_model="given")
     p["dust"] = [dict(x=g[0], y=g[1], z=g[2], a=g[3], q0=g[4] * QE) for g in GRAINS[:n_dust]]
@@ -86,6 +86,8 @@ def _force_case(n, n_dust, flags=0):
     o.set_ions(x, v, ids)
     acc_ref, fo_ref = o.forces()
     run = od.Run(p)
+    if variant is not None:
+        od.od_set_force_config(run.h, variant, 8, 0)
     run.set_ions(x, v, ids, next_id=n)
     _, _, a_gpu, id_gpu = run.get_ions()
     _, fo_gpu = run.dust_now()
@@ -93,10 +95,7 @@ def _force_case(n, n_dust, flags=0):
     return p, d, x, acc_ref, fo_ref, a_gpu, fo_gpu, id_gpu, ids
 
 
-@pytest.mark.parametrize("n,n_dust", [(1, 1), (2, 2), (33, 2), (255, 1), (256, 0), (257, 3), (2011, 1), (5000, 8)])
-def test_forces_on_injected_states(n, n_dust):
-    p, d, x, acc_ref, fo_ref, a_gpu, fo_gpu, id_gpu, ids = _force_case(n, n_dust)
-    assert np.array_equal(id_gpu, ids)
+def _check_forces(p, d, x, acc_ref, fo_ref, a_gpu, fo_gpu):
     kii = d["q"] ** 2 / (4 * math.pi * EPS0 * d["m"])
     psum, pbound = _pair_scale(x, d["lam"], kii)
     scale = psum + np.linalg.norm(acc_ref, axis=1)
@@ -106,11 +105,30 @@ def test_forces_on_injected_states(n, n_dust):
     assert np.linalg.norm(a_gpu - acc_ref) <= 1e-5 * np.linalg.norm(acc_ref)
     err = (dev - 2 * pbound) / scale
     assert err.max() < 1e-5, (err.max(), int(err.argmax()), (dev / scale).max())
-    if n_dust:
+    if len(p["dust"]):
         gs = _grain_scale(x, p["dust"], d["q"], d["lam"], [g["q0"] for g in p["dust"]])
         gs = gs + np.linalg.norm(fo_ref, axis=1)
         gerr = np.linalg.norm(fo_gpu - fo_ref, axis=1) / gs
         assert gerr.max() < 1e-5, gerr
+
+
+@pytest.mark.parametrize("n,n_dust", [(1, 1), (2, 2), (33, 2), (255, 1), (256, 0), (257, 3), (2011, 1), (5000, 8)])
+def test_forces_on_injected_states(n, n_dust):
+    p, d, x, acc_ref, fo_ref, a_gpu, fo_gpu, id_gpu, ids = _force_case(n, n_dust)
+    assert np.array_equal(id_gpu, ids)
+    _check_forces(p, d, x, acc_ref, fo_ref, a_gpu, fo_gpu)
+
+
+@pytest.mark.parametrize("variant", range(len(od.FORCE_VARIANTS)))
+@pytest.mark.parametrize("n", [1, 300, 2500, 4099])
+def test_every_pair_kernel_variant(variant, n):
+    """every variant, ordered-pair and symmetric, on one tile, several tiles and ragged
+    tails (the symmetric tiles hold 256-1024 ions); a second evaluation of the same state
+    gives the same bits (fixed summation order)"""
+    p, d, x, acc_ref, fo_ref, a_gpu, fo_gpu, id_gpu, ids = _force_case(n, 2, variant=variant)
+    _check_forces(p, d, x, acc_ref, fo_ref, a_gpu, fo_gpu)
+    _, _, _, _, _, a2, fo2, _, _ = _force_case(n, 2, variant=variant)
+    assert np.array_equal(a2, a_gpu) and np.array_equal(fo2, fo_gpu)
 
 
 def test_forces_without_ion_ion_term():
@@ -191,9 +209,18 @@ def test_tiny_200_steps_long_run_means():
     assert np.isclose(q[0], mg[0, 0]) and np.allclose(F[0], mg[0, 1:4] + mg[0, 4:7] + mg[0, 7:10] + mg[0, 10:13])
 
 
-def test_at_scale_sampled_forces():
+@pytest.mark.parametrize("config", ["tuned", "symmetric"])
+def test_at_scale_sampled_forces(config):
+    """the ~200,000-ion workload with the autotuner's choice (the benchmark's launch
+    configuration, same cache) and with the largest-tile symmetric kernel"""
     p = W.at_scale()
     run = od.Run(p)
+    if config == "tuned":
+        import torch
+
+        od.tune_cached(run.h, "%s|N=%d" % (torch.cuda.get_device_name(0), run.N))
+    else:
+        od.od_set_force_config(run.h, od.FORCE_VARIANTS.index((256, 4, 1)), 8, 0)
     run.step(3)
     x, v, a, ids = run.get_ions()
     rec, _ = run.series(2, 1)
