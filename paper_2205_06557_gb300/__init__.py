@@ -295,10 +295,12 @@ def od_selftest_wait_timeout(h, polls=2000):
     return lib().od_selftest_wait_timeout(h, int(polls))
 
 
-# (threads per block, targets per thread, symmetric) of each pair-kernel variant: the
-# ordered-pair kernel k_forces, then the symmetric (Newton III) kernel k_forces_sym
+# (threads per block, targets per thread, kind) of each pair-kernel variant: kind 0 the
+# ordered-pair kernel k_forces, 1 the symmetric (Newton III) kernel k_forces_sym, 2 the
+# symmetric kernel on packed FP32 pairs k_forces_sym2
 FORCE_VARIANTS = ((64, 1, 0), (64, 2, 0), (128, 2, 0), (128, 4, 0), (256, 2, 0), (256, 4, 0), (128, 8, 0),
-                  (64, 8, 0), (128, 2, 1), (128, 4, 1), (256, 2, 1), (256, 4, 1))
+                  (64, 8, 0), (128, 2, 1), (128, 4, 1), (256, 2, 1), (256, 4, 1), (128, 2, 2), (128, 4, 2),
+                  (256, 2, 2), (256, 4, 2))
 
 
 def force_variant_shape(v):
@@ -308,7 +310,7 @@ def force_variant_shape(v):
 
 def force_variant_name(v):
     bt, ipt, sym = FORCE_VARIANTS[v]
-    return "k_forces%s<%d,%d>" % ("_sym" if sym else "", bt, ipt)
+    return "k_forces%s<%d,%d>" % (("", "_sym", "_sym2")[sym], bt, ipt)
 
 
 def od_get_force_config(h):

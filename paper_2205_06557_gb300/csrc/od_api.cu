@@ -516,16 +516,16 @@ ForceArgs plan_forces(int N, int v, int sms, int units_per_block, int bps_cap)
 }
 
 // untuned choice: ordered pairs for small runs (many small units spread over the SMs),
-// the symmetric kernel (half the pair evaluations) above 32k ions while its partial slots
-// (N_pad^2 / tile x 16 bytes) stay within 4 GB (512-ion tiles) or 16 GB (1024-ion tiles)
+// the packed symmetric kernel with 1024-ion tiles (half the pair evaluations; fastest at
+// 200k ions) above 32k ions while its partial slots (N_pad^2 / 1024 x 16 bytes) stay
+// within 16 GB, i.e. up to ~1.05 million ions
 int default_variant(int N)
 {
     if (N <= 4096) return 0;
     if (N <= 32768) return 2;
-    const int sym512 = 9, sym1024 = 11;  // k_forces_sym<128,4>, k_forces_sym<256,4>
+    const int sym2_1024 = 15;  // k_forces_sym2<256,4>
     const double n = (double)N + 1024.0;
-    if (n * n / 512.0 * 16.0 <= 4.0 * (1ull << 30)) return sym512;
-    if (n * n / 1024.0 * 16.0 <= 16.0 * (1ull << 30)) return sym1024;
+    if (n * n / 1024.0 * 16.0 <= 16.0 * (1ull << 30)) return sym2_1024;
     return 3;
 }
 

@@ -630,6 +630,182 @@ __global__ void __launch_bounds__(BT) k_forces_sym(const float4* __restrict__ fp
     }
 }
 
+// ---------------------------------------- packed FP32 pairs (f32x2, sm_100 family)
+// Two FP32 values in one 64-bit register pair; add/sub/mul/fma on both in one
+// instruction with the same IEEE round-to-nearest as the scalar forms.
+typedef unsigned long long f32x2;
+
+__device__ __forceinline__ f32x2 pk2(float a, float b)
+{
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+
+__device__ __forceinline__ void upk2(f32x2 v, float& a, float& b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v)); }
+
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b)
+{
+    f32x2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b)
+{
+    f32x2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b)
+{
+    f32x2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c)
+{
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+// pair_c3 for two pairs at once (same operations and rounding per lane of the pair)
+__device__ __forceinline__ f32x2 pair_c3x2(f32x2 dx, f32x2 dy, f32x2 dz)
+{
+    const f32x2 eps2 = pk2(1e-24f, 1e-24f), ln2 = pk2(0.69314718055994531f, 0.69314718055994531f);
+    f32x2 r2 = fma2(dx, dx, eps2);
+    r2 = fma2(dy, dy, r2);
+    r2 = fma2(dz, dz, r2);
+    float ra, rb;
+    upk2(r2, ra, rb);
+    const f32x2 ri = pk2(rsqrt_approx(ra), rsqrt_approx(rb));
+    float sa, sb;
+    upk2(mul2(r2, ri), sa, sb);
+    const f32x2 e = pk2(ex2_approx(-sa), ex2_approx(-sb));
+    return mul2(mul2(e, mul2(ri, ri)), add2(ri, ln2));
+}
+
+// Symmetric kernel with packed FP32 pairs: the same tile-pair units, slots and fixed
+// combine order as k_forces_sym, but the travelling packet holds two sources (the lane's
+// sources q*64 + lane and q*64 + 32 + lane of the group), each target is duplicated into
+// both halves of a pair, and every FP32 operation of the pair term acts on the two
+// sources in one instruction.  Source-side sums are accumulated with the target-side sign
+// and negated when the warps' sums are combined.
+template <int BT, int IPT>
+__global__ void __launch_bounds__(BT) k_forces_sym2(const float4* __restrict__ fpos, float4* __restrict__ part,
+                                                    ForceArgs F)
+{
+    constexpr int NW = BT / 32;
+    constexpr int TI = BT * IPT;
+    constexpr int SUB = 128;
+    static_assert(TI % SUB == 0 && (TI / SUB) % 2 == 0, "tile must hold an even number of combine steps");
+    __shared__ float s_acc[2][3][NW][SUB];
+    __shared__ float4 sj[BT];
+    const int T = F.JS;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int src = (lane + 1) & 31;
+    long long u = (long long)blockIdx.x * F.U / F.G;
+    const long long u_end = (long long)(blockIdx.x + 1) * F.U / F.G;
+    if (u >= u_end) return;
+    int I, J;
+    tri_unit(u, T, I, J);
+    for (; u < u_end; ++u) {
+        float xi[IPT], yi[IPT], zi[IPT], ax[IPT], ay[IPT], az[IPT];
+#pragma unroll
+        for (int k = 0; k < IPT; ++k) {
+            const float4 p = fpos[I * TI + k * BT + threadIdx.x];
+            xi[k] = p.x;
+            yi[k] = p.y;
+            zi[k] = p.z;
+            ax[k] = 0.f;
+            ay[k] = 0.f;
+            az[k] = 0.f;
+        }
+        if (I == J) {
+            pair_chunk<BT, IPT>(fpos, I * TI, I * TI + TI, xi, yi, zi, ax, ay, az, sj);
+        } else {
+            f32x2 xd[IPT], yd[IPT], zd[IPT], ax2[IPT], ay2[IPT], az2[IPT];
+#pragma unroll
+            for (int k = 0; k < IPT; ++k) {
+                xd[k] = pk2(xi[k], xi[k]);
+                yd[k] = pk2(yi[k], yi[k]);
+                zd[k] = pk2(zi[k], zi[k]);
+                ax2[k] = ay2[k] = az2[k] = 0ull;
+            }
+            const int jb = J * TI;
+            for (int sc = 0; sc < TI / SUB; ++sc) {
+                const int buf = sc & 1;
+#pragma unroll 1
+                for (int q = 0; q < SUB / 64; ++q) {
+                    const int j0 = jb + sc * SUB + q * 64 + lane;
+                    const float4 pa = __ldg(fpos + j0), pb = __ldg(fpos + j0 + 32);
+                    f32x2 xj = pk2(pa.x, pb.x), yj = pk2(pa.y, pb.y), zj = pk2(pa.z, pb.z);
+                    f32x2 bx = 0ull, by = 0ull, bz = 0ull;
+#pragma unroll 2
+                    for (int r = 0; r < 32; ++r) {
+#pragma unroll
+                        for (int k = 0; k < IPT; ++k) {
+                            const f32x2 dx = sub2(xj, xd[k]), dy = sub2(yj, yd[k]), dz = sub2(zj, zd[k]);
+                            const f32x2 c3 = pair_c3x2(dx, dy, dz);
+                            ax2[k] = fma2(c3, dx, ax2[k]);
+                            ay2[k] = fma2(c3, dy, ay2[k]);
+                            az2[k] = fma2(c3, dz, az2[k]);
+                            bx = fma2(c3, dx, bx);
+                            by = fma2(c3, dy, by);
+                            bz = fma2(c3, dz, bz);
+                        }
+                        xj = __shfl_sync(0xffffffffu, xj, src);
+                        yj = __shfl_sync(0xffffffffu, yj, src);
+                        zj = __shfl_sync(0xffffffffu, zj, src);
+                        bx = __shfl_sync(0xffffffffu, bx, src);
+                        by = __shfl_sync(0xffffffffu, by, src);
+                        bz = __shfl_sync(0xffffffffu, bz, src);
+                    }
+                    float l0, h0;
+                    upk2(bx, l0, h0);
+                    s_acc[buf][0][w][q * 64 + lane] = l0;
+                    s_acc[buf][0][w][q * 64 + 32 + lane] = h0;
+                    upk2(by, l0, h0);
+                    s_acc[buf][1][w][q * 64 + lane] = l0;
+                    s_acc[buf][1][w][q * 64 + 32 + lane] = h0;
+                    upk2(bz, l0, h0);
+                    s_acc[buf][2][w][q * 64 + lane] = l0;
+                    s_acc[buf][2][w][q * 64 + 32 + lane] = h0;
+                }
+                // one barrier per combine step (double buffer, as in k_forces_sym)
+                __syncthreads();
+                for (int j = threadIdx.x; j < SUB; j += BT) {
+                    float sx = 0.f, sy = 0.f, sz = 0.f;
+#pragma unroll
+                    for (int ww = 0; ww < NW; ++ww) {
+                        sx += s_acc[buf][0][ww][j];
+                        sy += s_acc[buf][1][ww][j];
+                        sz += s_acc[buf][2][ww][j];
+                    }
+                    part[(long long)I * F.n_pad + jb + sc * SUB + j] = make_float4(-sx, -sy, -sz, 0.f);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < IPT; ++k) {
+                float l0, h0;
+                upk2(ax2[k], l0, h0);
+                ax[k] = l0 + h0;
+                upk2(ay2[k], l0, h0);
+                ay[k] = l0 + h0;
+                upk2(az2[k], l0, h0);
+                az[k] = l0 + h0;
+            }
+        }
+        float4* out = part + (long long)J * F.n_pad + I * TI + threadIdx.x;
+#pragma unroll
+        for (int k = 0; k < IPT; ++k) out[k * BT] = make_float4(ax[k], ay[k], az[k], 0.f);
+        if (++J == T) J = ++I;
+    }
+}
+
 // One (target tile t, source chunk c) unit written to partial slot c (batched launch,
 // where every unit is its own task and a tile's W = JS slots are its chunks).
 template <int BT, int IPT>

@@ -213,10 +213,12 @@ int launch_push_scan(const Phys& P, const Bufs& B, cudaStream_t s)
 }
 
 // pair-kernel variants (threads per block, targets per thread): ordered-pair kernels
-// k_forces, then symmetric ones k_forces_sym; targets per tile BT * IPT never exceed
-// 1024, the padding granularity of the position buffer
+// k_forces, symmetric ones k_forces_sym, then symmetric ones on packed FP32 pairs
+// k_forces_sym2; targets per tile BT * IPT never exceed 1024, the padding granularity of
+// the position buffer
 #define OD_FORCE_VARIANTS(X) X(64, 1) X(64, 2) X(128, 2) X(128, 4) X(256, 2) X(256, 4) X(128, 8) X(64, 8)
 #define OD_SYM_VARIANTS(X) X(128, 2) X(128, 4) X(256, 2) X(256, 4)
+#define OD_SYM2_VARIANTS(X) X(128, 2) X(128, 4) X(256, 2) X(256, 4)
 
 static const ForceVariant kVariants[] = {
 #define OD_V(bt, ipt) {bt, ipt, 0},
@@ -224,6 +226,9 @@ static const ForceVariant kVariants[] = {
 #undef OD_V
 #define OD_V(bt, ipt) {bt, ipt, 1},
     OD_SYM_VARIANTS(OD_V)
+#undef OD_V
+#define OD_V(bt, ipt) {bt, ipt, 2},
+    OD_SYM2_VARIANTS(OD_V)
 #undef OD_V
 };
 
@@ -238,6 +243,9 @@ static void* variant_fn(int v)
 #undef OD_V
 #define OD_V(bt, ipt) (void*)k_forces_sym<bt, ipt>,
         OD_SYM_VARIANTS(OD_V)
+#undef OD_V
+#define OD_V(bt, ipt) (void*)k_forces_sym2<bt, ipt>,
+        OD_SYM2_VARIANTS(OD_V)
 #undef OD_V
     };
     return fns[v];
@@ -267,6 +275,13 @@ int launch_forces(const Phys& P, const Bufs& B, const ForceArgs& F, int v, cudaS
         return ck(cudaGetLastError());                               \
     }
     OD_SYM_VARIANTS(OD_V)
+#undef OD_V
+#define OD_V(bt, ipt)                                                 \
+    if (v == idx++) {                                                 \
+        k_forces_sym2<bt, ipt><<<F.G, bt, 0, s>>>(B.fpos, B.part, F); \
+        return ck(cudaGetLastError());                                \
+    }
+    OD_SYM2_VARIANTS(OD_V)
 #undef OD_V
     return (int)cudaErrorInvalidValue;
 }
