@@ -72,6 +72,19 @@ def workload(name, seed):
     return W.at_scale(seed=seed), "ion flow past one 20 um grain, ~200,000 ions (R=0.9267 mm, H=1.853 mm)"
 
 
+def job_totals(dist, t_ms, units, device):
+    """(max over ranks of the timed region in ms, units all ranks processed): replicas
+    run independently, so the job takes as long as its slowest rank"""
+    import torch
+
+    tt = torch.tensor([float(t_ms)], dtype=torch.float64, device=device)
+    uu = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    if dist:
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        dist.all_reduce(uu, op=dist.ReduceOp.SUM)
+    return float(tt.item()), float(uu.item())
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -230,13 +243,7 @@ def run_ours(args):
     t_ms = sum(a.elapsed_time(b) for a, b in ev)
     kms, kn = od.od_kernel_times(run.h)
     od.od_set_profiling(run.h, 0)
-    tt = torch.tensor([t_ms], dtype=torch.float64, device="cuda")
-    units = torch.tensor([float(N) * (N - 1) * args.steps], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        dist.all_reduce(units, op=dist.ReduceOp.SUM)
-    t_max = float(tt.item())
-    pairs = float(units.item())
+    t_max, pairs = job_totals(dist, t_ms, float(N) * (N - 1) * args.steps, "cuda")
     value = pairs / (t_max / 1e3)
 
     # end to end through the ABI with host buffers: upload state, one step, read back
