@@ -397,11 +397,16 @@ def od_batch_run(b, r):
     return ctypes.c_void_p(lib().od_batch_run(b, int(r)))
 
 
+BATCH_TPT = (1, 2, 4)
+BATCH_CHUNKS = (2048, 4096, 8192, 0)  # 0: symmetric tile pairs
+
+
 def od_batch_tune(b, reps=2):
-    ms = np.zeros(9)
+    """(ms[targets per thread][chunk] as BATCH_TPT x BATCH_CHUNKS, best tpt, best chunk)"""
+    ms = np.zeros(12)
     bi, bj = ctypes.c_int(), ctypes.c_int()
     _bcheck(lib().od_batch_tune(b, int(reps), _ptr(ms), ctypes.byref(bi), ctypes.byref(bj)), b)
-    return ms.reshape(3, 3), bi.value, bj.value
+    return ms.reshape(3, 4), bi.value, bj.value
 
 
 def od_batch_set_config(b, targets_per_thread, chunk):

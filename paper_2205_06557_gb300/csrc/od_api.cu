@@ -1130,12 +1130,13 @@ struct od_batch {
     bool own_stream = false;
     RunDesc* d_runs = nullptr;
     int2* d_tasks = nullptr;
-    int2* d_tasks_f = nullptr;  // pair units only (tuning)
+    int2* d_tasks_f = nullptr;          // tuning: pair units, then kick tiles
     unsigned long long* d_done = nullptr;
+    unsigned long long* d_done_f = nullptr;  // phase counters of the tuning launches
     BatchCtrl* d_bc = nullptr;
     BatchCtrl* d_bc_f = nullptr;
     long long T = 0, T_f = 0;
-    int4 phase_end{0, 0, 0, 0};
+    int4 phase_end{0, 0, 0, 0}, phase_end_f{0, 0, 0, 0};
     int ipt = 2, jc = 4096, grid = 1, sms = 1;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -1197,7 +1198,10 @@ int batch_build(od_batch* b)
     b->phase_end = make_int4((int)tA.size(), (int)(tA.size() + tF.size()), (int)(tA.size() + tF.size() + tK.size()),
                              (int)all.size());
     b->T = (long long)all.size();
-    b->T_f = (long long)tF.size();
+    std::vector<int2> fk(tF);
+    fk.insert(fk.end(), tK.begin(), tK.end());
+    b->phase_end_f = make_int4(0, (int)tF.size(), (int)fk.size(), (int)fk.size());
+    b->T_f = (long long)fk.size();
     cudaFree(b->d_runs);
     cudaFree(b->d_tasks);
     cudaFree(b->d_tasks_f);
@@ -1205,11 +1209,11 @@ int batch_build(od_batch* b)
     b->d_tasks = b->d_tasks_f = nullptr;
     OD_BCK(b, cudaMalloc(&b->d_runs, sizeof(RunDesc) * R));
     OD_BCK(b, cudaMalloc(&b->d_tasks, sizeof(int2) * std::max<size_t>(all.size(), 1)));
-    OD_BCK(b, cudaMalloc(&b->d_tasks_f, sizeof(int2) * std::max<size_t>(tF.size(), 1)));
+    OD_BCK(b, cudaMalloc(&b->d_tasks_f, sizeof(int2) * std::max<size_t>(fk.size(), 1)));
     OD_BCK(b, cudaMemcpyAsync(b->d_runs, desc.data(), sizeof(RunDesc) * R, cudaMemcpyHostToDevice, b->stream));
     OD_BCK(b, cudaMemcpyAsync(b->d_tasks, all.data(), sizeof(int2) * all.size(), cudaMemcpyHostToDevice, b->stream));
-    if (!tF.empty())
-        OD_BCK(b, cudaMemcpyAsync(b->d_tasks_f, tF.data(), sizeof(int2) * tF.size(), cudaMemcpyHostToDevice, b->stream));
+    if (!fk.empty())
+        OD_BCK(b, cudaMemcpyAsync(b->d_tasks_f, fk.data(), sizeof(int2) * fk.size(), cudaMemcpyHostToDevice, b->stream));
     b->grid = (int)std::max(1ll, std::min<long long>((long long)batch_blocks_per_sm(b->ipt) * b->sms, b->T));
     OD_BCK(b, cudaStreamSynchronize(b->stream));
     b->graph_ok = false;
@@ -1227,6 +1231,7 @@ void batch_free(od_batch* b)
     cudaFree(b->d_tasks);
     cudaFree(b->d_tasks_f);
     cudaFree(b->d_done);
+    cudaFree(b->d_done_f);
     cudaFree(b->d_bc);
     cudaFree(b->d_bc_f);
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
@@ -1300,6 +1305,7 @@ int od_create_batch(const od_params* ps, int32_t R, od_batch** out)
         b->runs.push_back(h);
     }
     if (cudaMalloc(&b->d_done, sizeof(unsigned long long) * 3 * R) != cudaSuccess ||
+        cudaMalloc(&b->d_done_f, sizeof(unsigned long long) * 3 * R) != cudaSuccess ||
         cudaMalloc(&b->d_bc, sizeof(BatchCtrl)) != cudaSuccess || cudaMalloc(&b->d_bc_f, sizeof(BatchCtrl)) != cudaSuccess ||
         cudaEventCreate(&b->e0) != cudaSuccess || cudaEventCreate(&b->e1) != cudaSuccess) {
         b->err = "batch allocation failed";
@@ -1351,35 +1357,41 @@ od_handle* od_batch_run(od_batch* b, int32_t r)
 
 int od_batch_size(const od_batch* b) { return b ? (int)b->runs.size() : 0; }
 
+// one tuning launch of the current plan: every run's pair units, then its kick tiles in
+// forces-only mode (fresh counters per configuration)
+static int batch_tune_launch(od_batch* b, int grid)
+{
+    const int lrc = launch_batch(b->ipt, grid, b->d_runs, b->d_tasks_f, b->phase_end_f, b->T_f, b->d_bc_f,
+                                 b->d_done_f, (int)b->runs.size(), SPIN_LIMIT, 1, b->stream);
+    return lrc ? bfail(b, OD_ECUDA, "batch tune launch failed") : OD_OK;
+}
+
 int od_batch_tune(od_batch* b, int reps, double* ms, int* best_ipt, int* best_jc)
 {
     if (!b || reps < 1) return bfail(b, OD_EINVAL, "bad batch or repetition count");
     static const int ipts[3] = {1, 2, 4};
-    static const int jcs[3] = {2048, 4096, 8192};
+    static const int jcs[4] = {2048, 4096, 8192, 0};  // 0: symmetric tile pairs
     double best = 1e300;
     int bi = b->ipt, bj = b->jc;
+    const int R = (int)b->runs.size();
     for (int a = 0; a < 3; ++a)
-        for (int c = 0; c < 3; ++c) {
+        for (int c = 0; c < 4; ++c) {
             b->ipt = ipts[a];
             b->jc = jcs[c];
             int rc = batch_build(b);
             if (rc) return rc;
             OD_BCK(b, cudaMemsetAsync(b->d_bc_f, 0, sizeof(BatchCtrl), b->stream));
+            OD_BCK(b, cudaMemsetAsync(b->d_done_f, 0, sizeof(unsigned long long) * 3 * R, b->stream));
             const int grid = (int)std::max(1ll, std::min<long long>((long long)batch_blocks_per_sm(b->ipt) * b->sms, b->T_f));
-            const int R = (int)b->runs.size();
-            int lrc = launch_batch(b->ipt, grid, b->d_runs, b->d_tasks_f, b->phase_end, b->T_f, b->d_bc_f, b->d_done, R,
-                                   SPIN_LIMIT, 1, b->stream);
-            if (lrc) return bfail(b, OD_ECUDA, "batch tune launch failed");
+            if ((rc = batch_tune_launch(b, grid))) return rc;
             OD_BCK(b, cudaEventRecord(b->e0, b->stream));
             for (int i = 0; i < reps; ++i)
-                if ((lrc = launch_batch(b->ipt, grid, b->d_runs, b->d_tasks_f, b->phase_end, b->T_f, b->d_bc_f, b->d_done,
-                                        R, SPIN_LIMIT, 1, b->stream)))
-                    return bfail(b, OD_ECUDA, "batch tune launch failed");
+                if ((rc = batch_tune_launch(b, grid))) return rc;
             OD_BCK(b, cudaEventRecord(b->e1, b->stream));
             OD_BCK(b, cudaEventSynchronize(b->e1));
             float t = 0.f;
             OD_BCK(b, cudaEventElapsedTime(&t, b->e0, b->e1));
-            if (ms) ms[a * 3 + c] = t / reps;
+            if (ms) ms[a * 4 + c] = t / reps;
             if (t / reps < best) {
                 best = t / reps;
                 bi = ipts[a];
@@ -1390,6 +1402,14 @@ int od_batch_tune(od_batch* b, int reps, double* ms, int* best_ipt, int* best_jc
     b->jc = bj;
     int rc = batch_build(b);
     if (rc) return rc;
+    // the accelerations left by the timing belong to other plans: evaluate them again
+    // with the chosen one
+    OD_BCK(b, cudaMemsetAsync(b->d_bc_f, 0, sizeof(BatchCtrl), b->stream));
+    OD_BCK(b, cudaMemsetAsync(b->d_done_f, 0, sizeof(unsigned long long) * 3 * R, b->stream));
+    if ((rc = batch_tune_launch(b, (int)std::max(1ll, std::min<long long>((long long)batch_blocks_per_sm(b->ipt) * b->sms,
+                                                                            b->T_f)))))
+        return rc;
+    if ((rc = batch_check(b))) return rc;
     if (best_ipt) *best_ipt = bi;
     if (best_jc) *best_jc = bj;
     return OD_OK;
@@ -1397,7 +1417,8 @@ int od_batch_tune(od_batch* b, int reps, double* ms, int* best_ipt, int* best_jc
 
 int od_batch_set_config(od_batch* b, int ipt, int jc)
 {
-    if (!b || (ipt != 1 && ipt != 2 && ipt != 4) || jc < 256) return bfail(b, OD_EINVAL, "bad batch configuration");
+    if (!b || (ipt != 1 && ipt != 2 && ipt != 4) || (jc != 0 && jc < 256))
+        return bfail(b, OD_EINVAL, "bad batch configuration");
     b->ipt = ipt;
     b->jc = jc;
     return batch_build(b);

@@ -30,14 +30,18 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64c(const unsigned lon
     return v;
 }
 
-// phase_end: cumulative task-index ends of phases 0..3; forces_only: tuning launches
-// that run only pair units and skip the dependency waits
+// phase_end: cumulative task-index ends of phases 0..3.  tune = 1: a tuning launch whose
+// task list holds only pair units and kick tiles; the pair units do not wait, the kick
+// tiles wait for their run's pair units as in a step (on the tuning launch's own counters)
+// and evaluate accelerations only (kick mode 1: no velocity update, no collisions), so the
+// runs' states are not changed.
 template <int IPT>
 __global__ void __launch_bounds__(BATCH_BT, 2)
     k_batch_step(const RunDesc* __restrict__ runs, const int2* __restrict__ tasks, int4 phase_end, long long T,
-                 BatchCtrl* bc, unsigned long long* done, int R, long long spin_limit, int forces_only)
+                 BatchCtrl* bc, unsigned long long* done, int R, long long spin_limit, int tune)
 {
     __shared__ float4 sj[BATCH_BT];
+    __shared__ float s_acc[2][3][BATCH_BT / 32][SYM_SUB];
     __shared__ long long s_task;
     __shared__ int s_timeout;
     const unsigned long long bstep = bc->step;
@@ -51,8 +55,8 @@ __global__ void __launch_bounds__(BATCH_BT, 2)
         if (t >= T) break;
         const int2 tk = tasks[t];
         const RunDesc& d = runs[tk.x];
-        const int phase = forces_only ? 1 : (t < phase_end.x ? 0 : t < phase_end.y ? 1 : t < phase_end.z ? 2 : 3);
-        if (phase > 0 && !forces_only) {
+        const int phase = t < phase_end.x ? 0 : t < phase_end.y ? 1 : t < phase_end.z ? 2 : 3;
+        if (phase > 1 || (phase == 1 && !tune)) {
             // wait for the previous phase of this run
             if (threadIdx.x == 0) {
                 const unsigned long long per = phase == 1 ? (unsigned long long)d.nA
@@ -77,14 +81,22 @@ __global__ void __launch_bounds__(BATCH_BT, 2)
         }
         switch (phase) {
         case 0: push_scan_body<BATCH_BT>(d.P, d.B, d.nA, 1.4426950408889634 * d.P.lam_inv, tk.y); break;
-        case 1: forces_unit<BATCH_BT, IPT>(d.B.fpos, d.B.part, d.F, tk.y / d.F.JS, tk.y % d.F.JS, sj); break;
-        case 2: kick_body<BATCH_BT>(d.P, d.B, d.F, 0, tk.y); break;
+        case 1:
+            if (d.F.sym) {
+                int I, J;
+                tri_unit(tk.y, d.F.JS, I, J);
+                sym2_unit<BATCH_BT, IPT>(d.B.fpos, d.B.part, d.F, I, J, s_acc, sj);
+            } else {
+                forces_unit<BATCH_BT, IPT>(d.B.fpos, d.B.part, d.F, tk.y / d.F.JS, tk.y % d.F.JS, sj);
+            }
+            break;
+        case 2: kick_body<BATCH_BT>(d.P, d.B, d.F, tune ? 1 : 0, tk.y); break;
         default: dust_body(d.P, d.B, d.nK, 0); break;
         }
         // publish completion of this task to the run's phase counter
         __threadfence();
         __syncthreads();
-        if (threadIdx.x == 0 && phase < 3 && !forces_only) atomicAdd(done + (long long)phase * R + tk.x, 1ull);
+        if (threadIdx.x == 0 && phase < 3) atomicAdd(done + (long long)phase * R + tk.x, 1ull);
     }
     if (threadIdx.x == 0) {
         __threadfence();
@@ -112,17 +124,17 @@ int batch_blocks_per_sm(int ipt)
 }
 
 int launch_batch(int ipt, int grid, const RunDesc* runs, const int2* tasks, int4 phase_end, long long T,
-                 BatchCtrl* bc, unsigned long long* done, int R, long long spin_limit, int forces_only, cudaStream_t s)
+                 BatchCtrl* bc, unsigned long long* done, int R, long long spin_limit, int tune, cudaStream_t s)
 {
     switch (ipt) {
     case 1:
-        k_batch_step<1><<<grid, BATCH_BT, 0, s>>>(runs, tasks, phase_end, T, bc, done, R, spin_limit, forces_only);
+        k_batch_step<1><<<grid, BATCH_BT, 0, s>>>(runs, tasks, phase_end, T, bc, done, R, spin_limit, tune);
         break;
     case 2:
-        k_batch_step<2><<<grid, BATCH_BT, 0, s>>>(runs, tasks, phase_end, T, bc, done, R, spin_limit, forces_only);
+        k_batch_step<2><<<grid, BATCH_BT, 0, s>>>(runs, tasks, phase_end, T, bc, done, R, spin_limit, tune);
         break;
     default:
-        k_batch_step<4><<<grid, BATCH_BT, 0, s>>>(runs, tasks, phase_end, T, bc, done, R, spin_limit, forces_only);
+        k_batch_step<4><<<grid, BATCH_BT, 0, s>>>(runs, tasks, phase_end, T, bc, done, R, spin_limit, tune);
         break;
     }
     const cudaError_t e = cudaGetLastError();
@@ -130,13 +142,25 @@ int launch_batch(int ipt, int grid, const RunDesc* runs, const int2* tasks, int4
 }
 
 // the pair partition of one run inside a batch: tiles of BATCH_BT * ipt targets, source
-// chunks of jc, every unit its own task (G = U, slot = chunk)
+// chunks of jc, every unit its own task (G = U, slot = chunk); jc = 0 selects the
+// symmetric tile pairs of the packed kernel
 ForceArgs batch_plan(int N, int ipt, int jc)
 {
     ForceArgs F{};
     F.TI = BATCH_BT * ipt;
     F.n_pad = N == 0 ? 0 : (N + F.TI - 1) / F.TI * F.TI;
     if (F.n_pad == 0) return F;
+    if (jc == 0) {
+        // symmetric tile pairs (I, J >= I), one slot per tile for every ion
+        const int T = F.n_pad / F.TI;
+        F.sym = 1;
+        F.JC = F.TI;
+        F.JS = T;
+        F.W = T;
+        F.U = (long long)T * (T + 1) / 2;
+        F.G = (int)F.U;
+        return F;
+    }
     F.JC = std::max(BATCH_BT, std::min(jc, F.n_pad) / BATCH_BT * BATCH_BT);
     F.JS = (F.n_pad + F.JC - 1) / F.JC;
     F.U = (long long)(F.n_pad / F.TI) * F.JS;

@@ -688,121 +688,133 @@ __device__ __forceinline__ f32x2 pair_c3x2(f32x2 dx, f32x2 dy, f32x2 dz)
     return mul2(mul2(e, mul2(ri, ri)), add2(ri, ln2));
 }
 
-// Symmetric kernel with packed FP32 pairs: the same tile-pair units, slots and fixed
-// combine order as k_forces_sym, but the travelling packet holds two sources (the lane's
-// sources q*64 + lane and q*64 + 32 + lane of the group), each target is duplicated into
-// both halves of a pair, and every FP32 operation of the pair term acts on the two
-// sources in one instruction.  Source-side sums are accumulated with the target-side sign
-// and negated when the warps' sums are combined.
+constexpr int SYM_SUB = 128;  // sources per combine step of the symmetric kernels
+
+// One tile-pair unit (I, J >= I) of the symmetric kernel with packed FP32 pairs: the same
+// units, slots and fixed combine order as k_forces_sym, but the travelling packet holds
+// two sources (the lane's sources q*64 + lane and q*64 + 32 + lane of the group), each
+// target is duplicated into both halves of a pair, and every FP32 operation of the pair
+// term acts on the two sources in one instruction.  Source-side sums are accumulated
+// with the target-side sign and negated when the warps' sums are combined.  Every unit
+// starts on combine buffer 0 and ends on buffer 1, so consecutive units need no barrier
+// between them beyond the one per combine step.
+template <int BT, int IPT>
+__device__ __forceinline__ void sym2_unit(const float4* __restrict__ fpos, float4* __restrict__ part,
+                                          const ForceArgs& F, int I, int J, float (&s_acc)[2][3][BT / 32][SYM_SUB],
+                                          float4* sj)
+{
+    constexpr int NW = BT / 32;
+    constexpr int TI = BT * IPT;
+    static_assert(TI % SYM_SUB == 0 && (TI / SYM_SUB) % 2 == 0, "tile must hold an even number of combine steps");
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int src = (lane + 1) & 31;
+    float xi[IPT], yi[IPT], zi[IPT], ax[IPT], ay[IPT], az[IPT];
+#pragma unroll
+    for (int k = 0; k < IPT; ++k) {
+        const float4 p = fpos[I * TI + k * BT + threadIdx.x];
+        xi[k] = p.x;
+        yi[k] = p.y;
+        zi[k] = p.z;
+        ax[k] = 0.f;
+        ay[k] = 0.f;
+        az[k] = 0.f;
+    }
+    if (I == J) {
+        pair_chunk<BT, IPT>(fpos, I * TI, I * TI + TI, xi, yi, zi, ax, ay, az, sj);
+    } else {
+        f32x2 xd[IPT], yd[IPT], zd[IPT], ax2[IPT], ay2[IPT], az2[IPT];
+#pragma unroll
+        for (int k = 0; k < IPT; ++k) {
+            xd[k] = pk2(xi[k], xi[k]);
+            yd[k] = pk2(yi[k], yi[k]);
+            zd[k] = pk2(zi[k], zi[k]);
+            ax2[k] = ay2[k] = az2[k] = 0ull;
+        }
+        const int jb = J * TI;
+        for (int sc = 0; sc < TI / SYM_SUB; ++sc) {
+            const int buf = sc & 1;
+#pragma unroll 1
+            for (int q = 0; q < SYM_SUB / 64; ++q) {
+                const int j0 = jb + sc * SYM_SUB + q * 64 + lane;
+                const float4 pa = __ldg(fpos + j0), pb = __ldg(fpos + j0 + 32);
+                f32x2 xj = pk2(pa.x, pb.x), yj = pk2(pa.y, pb.y), zj = pk2(pa.z, pb.z);
+                f32x2 bx = 0ull, by = 0ull, bz = 0ull;
+#pragma unroll 2
+                for (int r = 0; r < 32; ++r) {
+#pragma unroll
+                    for (int k = 0; k < IPT; ++k) {
+                        const f32x2 dx = sub2(xj, xd[k]), dy = sub2(yj, yd[k]), dz = sub2(zj, zd[k]);
+                        const f32x2 c3 = pair_c3x2(dx, dy, dz);
+                        ax2[k] = fma2(c3, dx, ax2[k]);
+                        ay2[k] = fma2(c3, dy, ay2[k]);
+                        az2[k] = fma2(c3, dz, az2[k]);
+                        bx = fma2(c3, dx, bx);
+                        by = fma2(c3, dy, by);
+                        bz = fma2(c3, dz, bz);
+                    }
+                    xj = __shfl_sync(0xffffffffu, xj, src);
+                    yj = __shfl_sync(0xffffffffu, yj, src);
+                    zj = __shfl_sync(0xffffffffu, zj, src);
+                    bx = __shfl_sync(0xffffffffu, bx, src);
+                    by = __shfl_sync(0xffffffffu, by, src);
+                    bz = __shfl_sync(0xffffffffu, bz, src);
+                }
+                float l0, h0;
+                upk2(bx, l0, h0);
+                s_acc[buf][0][w][q * 64 + lane] = l0;
+                s_acc[buf][0][w][q * 64 + 32 + lane] = h0;
+                upk2(by, l0, h0);
+                s_acc[buf][1][w][q * 64 + lane] = l0;
+                s_acc[buf][1][w][q * 64 + 32 + lane] = h0;
+                upk2(bz, l0, h0);
+                s_acc[buf][2][w][q * 64 + lane] = l0;
+                s_acc[buf][2][w][q * 64 + 32 + lane] = h0;
+            }
+            // one barrier per combine step: the other buffer's readers (previous step)
+            // finished before they reached it
+            __syncthreads();
+            for (int j = threadIdx.x; j < SYM_SUB; j += BT) {
+                float sx = 0.f, sy = 0.f, sz = 0.f;
+#pragma unroll
+                for (int ww = 0; ww < NW; ++ww) {
+                    sx += s_acc[buf][0][ww][j];
+                    sy += s_acc[buf][1][ww][j];
+                    sz += s_acc[buf][2][ww][j];
+                }
+                part[(long long)I * F.n_pad + jb + sc * SYM_SUB + j] = make_float4(-sx, -sy, -sz, 0.f);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < IPT; ++k) {
+            float l0, h0;
+            upk2(ax2[k], l0, h0);
+            ax[k] = l0 + h0;
+            upk2(ay2[k], l0, h0);
+            ay[k] = l0 + h0;
+            upk2(az2[k], l0, h0);
+            az[k] = l0 + h0;
+        }
+    }
+    float4* out = part + (long long)J * F.n_pad + I * TI + threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < IPT; ++k) out[k * BT] = make_float4(ax[k], ay[k], az[k], 0.f);
+}
+
+// Persistent symmetric kernel on packed FP32 pairs: contiguous ranges of tile-pair units
 template <int BT, int IPT>
 __global__ void __launch_bounds__(BT) k_forces_sym2(const float4* __restrict__ fpos, float4* __restrict__ part,
                                                     ForceArgs F)
 {
-    constexpr int NW = BT / 32;
-    constexpr int TI = BT * IPT;
-    constexpr int SUB = 128;
-    static_assert(TI % SUB == 0 && (TI / SUB) % 2 == 0, "tile must hold an even number of combine steps");
-    __shared__ float s_acc[2][3][NW][SUB];
+    __shared__ float s_acc[2][3][BT / 32][SYM_SUB];
     __shared__ float4 sj[BT];
-    const int T = F.JS;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int src = (lane + 1) & 31;
     long long u = (long long)blockIdx.x * F.U / F.G;
     const long long u_end = (long long)(blockIdx.x + 1) * F.U / F.G;
     if (u >= u_end) return;
     int I, J;
-    tri_unit(u, T, I, J);
+    tri_unit(u, F.JS, I, J);
     for (; u < u_end; ++u) {
-        float xi[IPT], yi[IPT], zi[IPT], ax[IPT], ay[IPT], az[IPT];
-#pragma unroll
-        for (int k = 0; k < IPT; ++k) {
-            const float4 p = fpos[I * TI + k * BT + threadIdx.x];
-            xi[k] = p.x;
-            yi[k] = p.y;
-            zi[k] = p.z;
-            ax[k] = 0.f;
-            ay[k] = 0.f;
-            az[k] = 0.f;
-        }
-        if (I == J) {
-            pair_chunk<BT, IPT>(fpos, I * TI, I * TI + TI, xi, yi, zi, ax, ay, az, sj);
-        } else {
-            f32x2 xd[IPT], yd[IPT], zd[IPT], ax2[IPT], ay2[IPT], az2[IPT];
-#pragma unroll
-            for (int k = 0; k < IPT; ++k) {
-                xd[k] = pk2(xi[k], xi[k]);
-                yd[k] = pk2(yi[k], yi[k]);
-                zd[k] = pk2(zi[k], zi[k]);
-                ax2[k] = ay2[k] = az2[k] = 0ull;
-            }
-            const int jb = J * TI;
-            for (int sc = 0; sc < TI / SUB; ++sc) {
-                const int buf = sc & 1;
-#pragma unroll 1
-                for (int q = 0; q < SUB / 64; ++q) {
-                    const int j0 = jb + sc * SUB + q * 64 + lane;
-                    const float4 pa = __ldg(fpos + j0), pb = __ldg(fpos + j0 + 32);
-                    f32x2 xj = pk2(pa.x, pb.x), yj = pk2(pa.y, pb.y), zj = pk2(pa.z, pb.z);
-                    f32x2 bx = 0ull, by = 0ull, bz = 0ull;
-#pragma unroll 2
-                    for (int r = 0; r < 32; ++r) {
-#pragma unroll
-                        for (int k = 0; k < IPT; ++k) {
-                            const f32x2 dx = sub2(xj, xd[k]), dy = sub2(yj, yd[k]), dz = sub2(zj, zd[k]);
-                            const f32x2 c3 = pair_c3x2(dx, dy, dz);
-                            ax2[k] = fma2(c3, dx, ax2[k]);
-                            ay2[k] = fma2(c3, dy, ay2[k]);
-                            az2[k] = fma2(c3, dz, az2[k]);
-                            bx = fma2(c3, dx, bx);
-                            by = fma2(c3, dy, by);
-                            bz = fma2(c3, dz, bz);
-                        }
-                        xj = __shfl_sync(0xffffffffu, xj, src);
-                        yj = __shfl_sync(0xffffffffu, yj, src);
-                        zj = __shfl_sync(0xffffffffu, zj, src);
-                        bx = __shfl_sync(0xffffffffu, bx, src);
-                        by = __shfl_sync(0xffffffffu, by, src);
-                        bz = __shfl_sync(0xffffffffu, bz, src);
-                    }
-                    float l0, h0;
-                    upk2(bx, l0, h0);
-                    s_acc[buf][0][w][q * 64 + lane] = l0;
-                    s_acc[buf][0][w][q * 64 + 32 + lane] = h0;
-                    upk2(by, l0, h0);
-                    s_acc[buf][1][w][q * 64 + lane] = l0;
-                    s_acc[buf][1][w][q * 64 + 32 + lane] = h0;
-                    upk2(bz, l0, h0);
-                    s_acc[buf][2][w][q * 64 + lane] = l0;
-                    s_acc[buf][2][w][q * 64 + 32 + lane] = h0;
-                }
-                // one barrier per combine step (double buffer, as in k_forces_sym)
-                __syncthreads();
-                for (int j = threadIdx.x; j < SUB; j += BT) {
-                    float sx = 0.f, sy = 0.f, sz = 0.f;
-#pragma unroll
-                    for (int ww = 0; ww < NW; ++ww) {
-                        sx += s_acc[buf][0][ww][j];
-                        sy += s_acc[buf][1][ww][j];
-                        sz += s_acc[buf][2][ww][j];
-                    }
-                    part[(long long)I * F.n_pad + jb + sc * SUB + j] = make_float4(-sx, -sy, -sz, 0.f);
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < IPT; ++k) {
-                float l0, h0;
-                upk2(ax2[k], l0, h0);
-                ax[k] = l0 + h0;
-                upk2(ay2[k], l0, h0);
-                ay[k] = l0 + h0;
-                upk2(az2[k], l0, h0);
-                az[k] = l0 + h0;
-            }
-        }
-        float4* out = part + (long long)J * F.n_pad + I * TI + threadIdx.x;
-#pragma unroll
-        for (int k = 0; k < IPT; ++k) out[k * BT] = make_float4(ax[k], ay[k], az[k], 0.f);
-        if (++J == T) J = ++I;
+        sym2_unit<BT, IPT>(fpos, part, F, I, J, s_acc, sj);
+        if (++J == F.JS) J = ++I;
     }
 }
 

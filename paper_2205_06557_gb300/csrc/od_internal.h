@@ -141,7 +141,7 @@ constexpr int BATCH_TILE = 256;  // ions per scan / kick tile and threads per CT
 ForceArgs batch_plan(int N, int ipt, int jc);
 int batch_blocks_per_sm(int ipt);
 int launch_batch(int ipt, int grid, const RunDesc* runs, const int2* tasks, int4 phase_end, long long T,
-                 BatchCtrl* bc, unsigned long long* done, int R, long long spin_limit, int forces_only,
+                 BatchCtrl* bc, unsigned long long* done, int R, long long spin_limit, int tune,
                  cudaStream_t s);
 
 // host launchers (od_kernels.cu)

@@ -66,13 +66,30 @@ def test_batch_tuning_keeps_results():
     ps = _params()[:2]
     batch = od.Batch(ps)
     ms, ipt, jc = batch.tune(reps=1)
-    assert ms.min() > 0 and ipt in (1, 2, 4) and jc in (2048, 4096, 8192)
+    assert ms.shape == (3, 4) and ms.min() > 0 and ipt in (1, 2, 4) and jc in (2048, 4096, 8192, 0)
+    assert ms[od.BATCH_TPT.index(ipt), od.BATCH_CHUNKS.index(jc)] == ms.min()
     singles = [od.Run(p) for p in ps]
     batch.step(15)
     for s in singles:
         s.step(15)
     for r, s in zip(batch.runs, singles):
         _compare(r, s, 15)
+    batch.close()
+
+
+@pytest.mark.parametrize("tpt", [1, 2, 4])
+def test_batch_symmetric_plan_reproduces_single_runs(tpt):
+    """the batch's symmetric tile pairs (each unordered pair once) give the same events
+    and trajectories as the runs stepped alone"""
+    ps = _params()
+    batch = od.Batch(ps)
+    od.od_batch_set_config(batch.b, tpt, 0)
+    singles = [od.Run(p) for p in ps]
+    batch.step(20)
+    for s in singles:
+        s.step(20)
+    for r, s in zip(batch.runs, singles):
+        _compare(r, s, 20)
     batch.close()
 
 
