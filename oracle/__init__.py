@@ -48,6 +48,8 @@ class _Params(ctypes.Structure):
         ("grid_nz", ctypes.c_int32),
         ("quad_n", ctypes.c_int32),
         ("pad_", ctypes.c_int32),
+        ("r_cut", ctypes.c_double),
+        ("r_switch", ctypes.c_double),
     ]
 
 
@@ -114,6 +116,8 @@ def _to_struct(p):
     s.grid_nx = int(p.get("grid_nx", 0))
     s.grid_nz = int(p.get("grid_nz", 0))
     s.quad_n = int(p.get("quad_n", 0))
+    s.r_cut = float(p.get("r_cut", 0.0))
+    s.r_switch = float(p.get("r_switch", 0.0))
     return s
 
 

@@ -364,6 +364,7 @@ void orc_forces(const orc_state* s, int64_t i0, int64_t i1, double* acc, double*
     const double qm = p->Z * QE / p->m_i;                        /* q / m */
     const int ionion = !(p->flags & ORC_F_NO_IONION);
     const int eout = !(p->flags & ORC_F_NO_EOUT);
+    const int cut = p->r_cut > 0.0;
 #ifdef _OPENMP
 #pragma omp parallel for schedule(dynamic, 16)
 #endif
@@ -376,7 +377,16 @@ void orc_forces(const orc_state* s, int64_t i0, int64_t i1, double* acc, double*
                 if (j == i) continue;
                 double dx = xi - s->x[3 * j], dy = yi - s->x[3 * j + 1], dz = zi - s->x[3 * j + 2];
                 double r = sqrt(dx * dx + dy * dy + dz * dz);
+                if (cut && r >= p->r_cut) continue;
                 double f = (1.0 + r / lam) * exp(-r / lam) / (r * r * r);
+                if (cut && r > p->r_switch) {
+                    /* switched energy U S: force -(U' S + U S') r_hat, with U = exp(-r/lam)/r */
+                    const double w = p->r_cut - p->r_switch, x = (r - p->r_switch) / w;
+                    const double S = 1.0 - x * x * x * (10.0 - 15.0 * x + 6.0 * x * x);
+                    const double dS = -30.0 * x * x * (1.0 - x) * (1.0 - x) / w;
+                    const double U = exp(-r / lam) / r;
+                    f = f * S - U * dS / r;
+                }
                 ax += f * dx;
                 ay += f * dy;
                 az += f * dz;
@@ -502,6 +512,10 @@ orc_state* orc_create(const orc_params* pin, char* err, int errlen)
     }
     if (p->n_dust < 0 || p->n_dust > ORC_MAX_DUST) {
         set_err(err, errlen, "n_dust out of range");
+        return NULL;
+    }
+    if (p->r_cut > 0 && !(p->r_switch >= 0 && p->r_switch < p->r_cut)) {
+        set_err(err, errlen, "cutoff: need 0 <= r_switch < r_cut");
         return NULL;
     }
     if (p->mach < 0 || p->E_ext < 0 || p->nu < 0 || (p->mach > 0 && p->E_ext > 0) || (p->E_ext > 0 && p->nu <= 0)) {

@@ -59,6 +59,11 @@ typedef struct {
     int32_t grid_nx, grid_nz;   /* App. A grid, 0 => 40 */
     int32_t quad_n;             /* Gauss-Legendre points per segment, 0 => 48 */
     int32_t pad_;
+    /* ion-ion cutoff (Sec. 5: a switching function that vanishes beyond a fixed
+     * distance); r_cut <= 0 => none.  Between r_switch and r_cut the pair energy is
+     * multiplied by S(x) = 1 - 10 x^3 + 15 x^4 - 6 x^5, x = (r - r_switch) / (r_cut -
+     * r_switch); the force is minus the gradient of the switched energy. */
+    double r_cut, r_switch;
 } orc_params;
 
 typedef struct orc_state orc_state;
