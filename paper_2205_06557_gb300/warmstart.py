@@ -153,10 +153,35 @@ def steps_to_converge(q, q_ref, tol):
     return 0 if len(bad) == 0 else int(bad[-1]) + 1
 
 
-def evaluate(net, norm, plist, steps, tol=0.01, stream=None):
+def batch_se(x, nb=20):
+    """standard error of the mean of a correlated series by batch means (nb batches)"""
+    m = len(x) // nb
+    if m < 1:
+        return float("nan")
+    b = np.asarray(x[: m * nb], dtype=np.float64).reshape(nb, m).mean(1)
+    return float(b.std(ddof=1) / np.sqrt(nb))
+
+
+def steps_to_force(f, f_ref, se_ref, window, stride=250):
+    """steps that must be simulated before a window mean of the per-step force agrees
+    with the converged force: the smallest t + window such that the mean of f over
+    [t, t + window) is within 2 combined standard errors (batch means of that window and
+    se_ref) of f_ref; len(f) + 1 if no window qualifies"""
+    c = np.concatenate([[0.0], np.cumsum(np.asarray(f, dtype=np.float64))])
+    for t in range(0, len(f) - window + 1, stride):
+        m = (c[t + window] - c[t]) / window
+        se = np.hypot(batch_se(f[t: t + window]), se_ref)
+        if abs(m - f_ref) <= 2.0 * se:
+            return t + window
+    return len(f) + 1
+
+
+def evaluate(net, norm, plist, steps, tol=0.01, stream=None, details=False):
     """Held-out runs from q0 = 0, OML and network predictions, stepped in one batch.
     Returns per-strategy arrays of steps to converge (one per grain) and the initial
-    charge errors relative to the converged charge."""
+    charge errors relative to the converged charge; with details=True also the steps to
+    a converged axial force (window of steps/4, 2 standard errors) and the batch's
+    device time per step."""
     q_net = predict_q0(net, norm, plist)
     runs = []
     for p, qn in zip(plist, q_net):
@@ -168,18 +193,35 @@ def evaluate(net, norm, plist, steps, tol=0.01, stream=None):
             r["avg_start"] = steps - steps // 4 + 1
             runs.append(r)
     b = Batch(runs, stream=stream)
-    b.step(steps)
+    import time
+
+    t0 = time.perf_counter()
+    b.step(steps)  # synchronises on the error word at the end
+    t_step = (time.perf_counter() - t0) / steps
     res = {s: [] for s in ("zero", "oml", "net")}
+    resf = {s: [] for s in ("zero", "oml", "net")}
     err0 = {s: [] for s in ("zero", "oml", "net")}
+    window = steps // 4
     for i, p in enumerate(plist):
-        series = [b.runs[3 * i + j].series(1, steps)[0][:, :, 0] for j in range(3)]
-        tail = steps - steps // 4
-        # converged charge: last quarter of the runs started near it (OML and network)
+        recs = [b.runs[3 * i + j].series(1, steps)[0] for j in range(3)]
+        series = [r[:, :, 0] for r in recs]
+        # total axial force per step: orbit + grain-grain + collection + driving field
+        fz = [r[:, :, 3] + r[:, :, 6] + r[:, :, 9] + r[:, :, 12] for r in recs]
+        tail = steps - window
+        # converged charge and force: last quarter of the runs started near it (OML and
+        # network)
         q_ref = np.mean([s[tail:].mean(0) for s in series[1:]], axis=0)
         for j, strat in enumerate(("zero", "oml", "net")):
             q0 = np.array([g["q0"] for g in runs[3 * i + j]["dust"]])
             for k in range(len(p["dust"])):
                 res[strat].append(steps_to_converge(series[j][:, k], q_ref[k], tol))
                 err0[strat].append(abs(q0[k] - q_ref[k]) / abs(q_ref[k]))
+                if details:
+                    f_ref = 0.5 * (fz[1][tail:, k].mean() + fz[2][tail:, k].mean())
+                    se_ref = 0.5 * np.hypot(batch_se(fz[1][tail:, k]), batch_se(fz[2][tail:, k]))
+                    resf[strat].append(steps_to_force(fz[j][:, k], f_ref, se_ref, window))
     b.close()
-    return {s: np.array(v) for s, v in res.items()}, {s: np.array(v) for s, v in err0.items()}
+    out = ({s: np.array(v) for s, v in res.items()}, {s: np.array(v) for s, v in err0.items()})
+    if details:
+        out = out + ({s: np.array(v) for s, v in resf.items()}, t_step)
+    return out

@@ -40,6 +40,22 @@ def test_steps_to_converge():
     assert steps_to_converge(np.full(10, -1e5), -1e5, 0.01) == 0
 
 
+def test_force_convergence_criterion():
+    from paper_2205_06557_gb300.warmstart import batch_se, steps_to_force
+
+    rng = np.random.default_rng(1)
+    # white noise: batch-means SE equals sigma / sqrt(n)
+    x = rng.normal(0.0, 2.0, 200_000)
+    assert abs(batch_se(x) / (2.0 / np.sqrt(len(x))) - 1) < 0.4
+    # a relaxing mean plus noise: the first window that agrees starts after the transient
+    t = np.arange(40_000)
+    f = 5.0 + 3.0 * np.exp(-t / 2000.0) + rng.normal(0.0, 1.0, len(t))
+    n = steps_to_force(f, 5.0, 0.0, 10_000)
+    assert 10_000 < n < 30_000
+    # a series that never reaches the reference
+    assert steps_to_force(f + 1.0, 5.0, 0.0, 10_000) == len(f) + 1
+
+
 @pytest.mark.gpu
 def test_warm_start_pipeline_beats_zero_start():
     from paper_2205_06557_gb300 import warmstart as ws
