@@ -50,7 +50,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="scale", choices=["scale", "tiny", "chain", "sweep", "warmstart"])
+    ap.add_argument("--workload", default="scale", choices=["scale", "tiny", "chain", "sweep", "warmstart", "cutoff"])
+    ap.add_argument("--max-all-pairs-log2", type=int, default=20)
     ap.add_argument("--label-steps", type=int, default=60000)
     ap.add_argument("--train-iters", type=int, default=3000)
     ap.add_argument("--eval-runs", type=int, default=48)
@@ -376,9 +377,26 @@ def run_warmstart(args):
     t_train = time.perf_counter() - t0
     evalp = [ws.study_run(rank * 100_000 + 90_000 + s, args.eval_steps, **dom) for s in range(args.eval_runs)]
     t0 = time.perf_counter()
-    steps, err0 = ws.evaluate(net, norm, evalp, args.eval_steps, tol=0.01)
+    steps, err0, steps_f, t_bstep = ws.evaluate(net, norm, evalp, args.eval_steps, tol=0.01, details=True)
     t_eval = time.perf_counter() - t0
     dt = evalp[0]["dt"]
+    # the plain method one run at a time (q0 = OML): wall time per step of a single run
+    import paper_2205_06557_gb300 as od
+
+    single = od.Run(evalp[0])
+    single.step(200)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    single.step(2000)
+    t_single = (time.perf_counter() - t0) / 2000
+    single.close()
+    per_run = t_bstep / (3 * len(evalp))  # the evaluation batch holds 3 starts per run
+    wall = {"plain_single_run_zero_start": float(np.mean(steps["zero"])) * t_single,
+            "plain_single_run_oml_start": float(np.mean(steps["oml"])) * t_single,
+            "batched_network_start": float(np.mean(steps["net"])) * per_run}
+    wall_f = {"plain_single_run_zero_start": float(np.mean(steps_f["zero"])) * t_single,
+              "plain_single_run_oml_start": float(np.mean(steps_f["oml"])) * t_single,
+              "batched_network_start": float(np.mean(steps_f["net"])) * per_run}
     line = {"metric": "time-to-converged dust charge (steps to stay within 1%)", "unit": "steps",
             "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
             "config": {"workload": "~2,200-ion runs (n=2e14 m^-3, R=0.12 mm, H=0.24 mm), Ar+ 300 K, T_e 2 eV, "
@@ -394,10 +412,74 @@ def run_warmstart(args):
             "initial_charge_error_median": {k: float(np.median(v)) for k, v in err0.items()},
             "speedup_vs_zero": float(np.mean(steps["zero"]) / max(np.mean(steps["net"]), 1.0)),
             "speedup_vs_oml": float(np.mean(steps["oml"]) / max(np.mean(steps["net"]), 1.0)),
+            "force_steps_mean": {k: float(np.mean(v)) for k, v in steps_f.items()},
+            "force_criterion": "window mean of the total axial force over eval_steps/4 steps within 2 combined "
+                               "batch-means standard errors of the converged force (last quarter of the OML- and "
+                               "network-started runs); steps counted to the end of the first such window",
+            "wall_s_per_run_to_converged_charge": wall,
+            "wall_s_per_run_to_converged_force": wall_f,
+            "step_time_s": {"single_run": t_single, "batched_per_run": per_run},
+            "wall_speedup_charge_vs_plain_oml": wall["plain_single_run_oml_start"] / max(wall["batched_network_start"], 1e-30),
+            "wall_speedup_charge_vs_plain_zero": wall["plain_single_run_zero_start"] / max(wall["batched_network_start"], 1e-30),
+            "wall_speedup_force_vs_plain_oml": wall_f["plain_single_run_oml_start"] / max(wall_f["batched_network_start"], 1e-30),
             "train_loss_first_last": [float(losses[:50].mean()), float(losses[-50:].mean())],
             "validation_loss_best": float(vlosses.min()) if len(vlosses) else None,
             "wall_s": {"generate": t_gen, "train": t_train, "evaluate": t_eval}}
     net.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_cutoff(args):
+    """The cutoff's scaling at constant ion density (Sec. 5's second series): the
+    ~2,000-ion plasma in a tube of radius 0.2 mm whose length grows with N, one grain at
+    the centre; time per step with the cutoff (r_cut = 2 lambda_De, switching from
+    lambda_De) and with all pairs, and the exponent of t ~ N^beta fitted over the series."""
+    import torch
+
+    import paper_2205_06557_gb300 as od
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    rows = []
+    for e in range(15, 21):
+        n = 2 ** e
+        p = W.tiny(seed=rank)
+        p["H"] = n / (p["n_inf"] * math.pi * p["R"] ** 2)
+        p["n_ions"] = n
+        p["charge_model"] = "given"
+        row = {"n_ions": n, "H_m": p["H"]}
+        for mode in ("cutoff", "all_pairs"):
+            if mode == "all_pairs" and n > 2 ** args.max_all_pairs_log2:
+                continue
+            run = od.Run(p, stream=ctypes_stream(stream))
+            lam = run.info()["lam"]
+            if mode == "cutoff":
+                od.od_set_cutoff(run.h, 2 * lam, lam)
+            run.step(args.warmup)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            run.step(args.steps)
+            torch.cuda.synchronize()
+            row[mode + "_s_per_step"] = (time.perf_counter() - t0) / args.steps
+            run.close()
+        row["paper_v100_fit_s_per_run_of_3000_steps"] = 0.00016 * n ** 1.177
+        rows.append(row)
+    lg = lambda k: [(math.log(r["n_ions"]), math.log(r[k])) for r in rows if k in r and r["n_ions"] >= 2 ** 17]
+    fit = lambda pts: float(np.polyfit([a for a, _ in pts], [b for _, b in pts], 1)[0]) if len(pts) >= 2 else None
+    big = rows[-1]
+    line = {"metric": "time per step with the ion-ion cutoff at constant density", "unit": "s/step",
+            "value": big["cutoff_s_per_step"], "higher_is_better": False, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "data": "synthetic", "dtype": "f32",
+            "config": {"workload": "Ar+ 300 K, T_e 2 eV, n=4e13 m^-3, tube R=0.2 mm, H grown with N "
+                                   "(%.1f-%.1f mm), one 20 um grain, Mach 1, nu 1e6 /s" % (
+                                       1e3 * rows[0]["H_m"], 1e3 * rows[-1]["H_m"]),
+                       "r_cut": "2 lambda_De", "r_switch": "lambda_De", "n_ions": big["n_ions"]},
+            "series": rows, "beta_cutoff": fit(lg("cutoff_s_per_step")),
+            "beta_all_pairs": fit(lg("all_pairs_s_per_step")),
+            "ion_steps_per_s": big["n_ions"] / big["cutoff_s_per_step"]}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -411,6 +493,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "cutoff":
+        run_cutoff(args)
     elif args.workload == "sweep":
         run_sweep(args)
     elif args.workload == "warmstart":

@@ -146,6 +146,56 @@ int64_t od_get_ions(od_handle* h, double* x, double* v, double* a, uint64_t* id,
 int od_set_ions(od_handle* h, const double* x, const double* v, const double* a, const uint64_t* id,
                 int64_t n, uint64_t next_id);
 
+/* Ion-ion cutoff (Sec. 5: a switching function that is zero beyond a fixed cutoff
+ * distance, so that the cost grows far slower than N^2 in long domains).  The paper does
+ * not give the switching form; here the Yukawa pair energy is multiplied by
+ * S(x) = 1 - 10 x^3 + 15 x^4 - 6 x^5, x = (r - r_switch) / (r_cut - r_switch) on
+ * [r_switch, r_cut], S = 1 below and 0 above, and the pair force is minus the gradient of
+ * the switched energy (continuous, zero at r_cut).  The ion-grain forces, Eq. 1 and
+ * E_out are unchanged.  0 <= r_switch < r_cut (m); r_cut <= 0 switches the cutoff off.
+ * Every later force evaluation sorts the ions by z and visits only tile pairs whose
+ * bounding boxes come within r_cut (suited to the elongated domains of the paper's
+ * cutoff study); the call re-evaluates the forces of the current state.  At most
+ * 2,097,152 ions; OD_EINVAL when the partial sums would need more than 48 GB (a cutoff
+ * long against the domain) or on a batch member; od_tune is not available while the
+ * cutoff is on.  A step reports OD_EOVERFLOW if the ion density becomes so uneven that
+ * a tile's neighbours exceed the slots sized here (calling od_set_cutoff again resizes). */
+int od_set_cutoff(od_handle* h, double r_cut, double r_switch);
+
+/* Checkpoint and restart (the paper's runs last tens of thousands of steps, Sec. 4).
+ * od_save writes the whole state of a single run to a binary file: the creation
+ * parameters, the E_out coefficients, positions, velocities, ids and accelerations, the
+ * control block (step, next id, charges, window sums, counters) and every per-step
+ * record so far, plus the pair-kernel choice.  od_load creates a new run from such a
+ * file on cuda_stream (NULL: a stream owned by the library); continuing it gives the
+ * same results, bit for bit, as continuing the saved run on the same GPU model.  The file
+ * is in host byte order and tied to this library's layout: a foreign, truncated or
+ * inconsistent file is OD_EINVAL before any device work (then od_last_error(NULL)). */
+int od_save(od_handle* h, const char* path);
+int od_load(const char* path, void* cuda_stream, od_handle** out);
+/* number of grains of a run (>= 0), or a negative error code */
+int od_num_dust(od_handle* h);
+
+/* Ion dumps for external viewers (the paper's density pictures, Sec. 4, are made from
+ * such files): the current ions as extended XYZ (OD_DUMP_XYZ: count line, a properties
+ * line with step and time, then "I x y z vx vy vz id", SI) or CSV (OD_DUMP_CSV:
+ * id,x,y,z,vx,vy,vz), full FP64 precision. */
+#define OD_DUMP_XYZ 0
+#define OD_DUMP_CSV 1
+int od_write_ions(od_handle* h, const char* path, int32_t format);
+
+/* Time-averaged ion density n(r, z) on an nr x nz grid over r in [0, R), z in
+ * [-H/2, H/2] (the axisymmetric density maps of Sec. 4).  od_density_enable allocates
+ * and zeroes the counts (1 <= nr, nz <= 4096, nr nz <= 2^22; 0, 0 switches the map off)
+ * and every later od_step adds the ions' end-of-step positions (a binning kernel in the
+ * step; bins from FP64 positions with correctly rounded operations, integer counts).
+ * od_density_read copies counts[nz][nr] (uint64, host, may be NULL), the density
+ * density[nz][nr] = counts w / (samples V_bin) in m^-3 (host, may be NULL; V_bin the
+ * annulus volume) and the number of steps accumulated.  Single runs only (not batch
+ * members). */
+int od_density_enable(od_handle* h, int32_t nr, int32_t nz);
+int od_density_read(od_handle* h, uint64_t* counts, double* density, int64_t* samples);
+
 /* Derived constants (host double[32]): lambda_De, c_s, sig_i, sig_n, u, E, q, m, p_bottom,
  * p_top, p_side, T_bottom, T_bottom+top, T_coll, N, alpha[0..14] (at 15..29), capacity, SMs. */
 int od_info(od_handle* h, double* out);

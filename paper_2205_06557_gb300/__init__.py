@@ -116,6 +116,16 @@ def lib():
         L.od_batch_last_error.restype = ctypes.c_char_p
         for name in ("od_create_batch", "od_batch_step", "od_batch_size", "od_batch_tune", "od_batch_set_config"):
             getattr(L, name).restype = ctypes.c_int
+        L.od_set_cutoff.argtypes = [vp, ctypes.c_double, ctypes.c_double]
+        L.od_set_cutoff.restype = ctypes.c_int
+        L.od_save.argtypes = [vp, ctypes.c_char_p]
+        L.od_load.argtypes = [ctypes.c_char_p, vp, P(vp)]
+        L.od_num_dust.argtypes = [vp]
+        L.od_write_ions.argtypes = [vp, ctypes.c_char_p, i32]
+        L.od_density_enable.argtypes = [vp, i32, i32]
+        L.od_density_read.argtypes = [vp, vp, vp, vp]
+        for name in ("od_save", "od_load", "od_num_dust", "od_write_ions", "od_density_enable", "od_density_read"):
+            getattr(L, name).restype = ctypes.c_int
         L.od_oml_charge.argtypes = [P(od_params), ctypes.c_double, vp]
         L.od_oml_charge.restype = ctypes.c_int
         L.od_sur_create.argtypes = [ctypes.c_int, ctypes.c_uint64, vp, P(vp)]
@@ -272,6 +282,45 @@ def od_info(h):
     d["capacity"] = out[30]
     d["sms"] = out[31]
     return d
+
+
+DUMP_XYZ, DUMP_CSV = 0, 1
+
+
+def od_set_cutoff(h, r_cut, r_switch=0.0):
+    """ion-ion cutoff with the energy switching zone [r_switch, r_cut] (m); r_cut <= 0: off"""
+    return _check(lib().od_set_cutoff(h, float(r_cut), float(r_switch)), h)
+
+
+def od_save(h, path):
+    return _check(lib().od_save(h, os.fsencode(path)), h)
+
+
+def od_load(path, stream=None):
+    h = ctypes.c_void_p()
+    _check(lib().od_load(os.fsencode(path), stream, ctypes.byref(h)))
+    return h
+
+
+def od_num_dust(h):
+    return _check(lib().od_num_dust(h), h)
+
+
+def od_write_ions(h, path, fmt=DUMP_XYZ):
+    return _check(lib().od_write_ions(h, os.fsencode(path), int(fmt)), h)
+
+
+def od_density_enable(h, nr, nz):
+    return _check(lib().od_density_enable(h, int(nr), int(nz)), h)
+
+
+def od_density_read(h, nr, nz):
+    """(counts[nz, nr] uint64, density[nz, nr] m^-3, steps accumulated)"""
+    counts = np.zeros((nz, nr), dtype=np.uint64)
+    dens = np.zeros((nz, nr))
+    n = ctypes.c_int64()
+    _check(lib().od_density_read(h, _ptr(counts), _ptr(dens), ctypes.byref(n)), h)
+    return counts, dens, n.value
 
 
 def od_set_profiling(h, on):
@@ -434,6 +483,21 @@ class Run:
         r.D, r.h, r.owned = n_dust, h, False
         r.N = int(od_info(h)["N"])
         return r
+
+    @classmethod
+    def load(cls, path, stream=None):
+        """a run restored from a checkpoint written by save()"""
+        r = cls.__new__(cls)
+        r.h, r.owned = od_load(path, stream), True
+        r.D = od_num_dust(r.h)
+        r.N = int(od_info(r.h)["N"])
+        return r
+
+    def save(self, path):
+        od_save(self.h, path)
+
+    def write_ions(self, path, fmt=DUMP_XYZ):
+        od_write_ions(self.h, path, fmt)
 
     def step(self, n=1):
         od_step(self.h, n)

@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(BATCH_BT, 2)
             if (d.F.sym) {
                 int I, J;
                 tri_unit(tk.y, d.F.JS, I, J);
-                sym2_unit<BATCH_BT, IPT>(d.B.fpos, d.B.part, d.F, I, J, s_acc, sj);
+                sym2_unit<BATCH_BT, IPT>(d.B.fpos, d.B.part, d.F, I, J, s_acc, sj, J, I);
             } else {
                 forces_unit<BATCH_BT, IPT>(d.B.fpos, d.B.part, d.F, tk.y / d.F.JS, tk.y % d.F.JS, sj);
             }

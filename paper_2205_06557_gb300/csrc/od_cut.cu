@@ -1,0 +1,327 @@
+// Ion-ion forces with a cutoff (Sec. 5: a switching function that vanishes beyond a
+// fixed distance, so that distant ion pairs cost nothing).
+//
+// Every evaluation:
+//   1. the ions are sorted stably by z-slab (slab width a fraction of the cutoff): a
+//      counting sort whose blocks are single warps, so the rank of an ion among the
+//      ions of its slab in the same warp comes from __match_any_sync, and the order
+//      inside a slab is the ion order (deterministic);
+//   2. the sorted positions are cut into tiles of TI ions; each tile gets the bounding
+//      box of its ions;
+//   3. one CTA lists, for every tile, the tiles whose boxes come closer than the
+//      cutoff (neighbour lists, CSR) and the tile pairs (I, J >= I) among them;
+//   4. persistent CTAs evaluate those tile pairs with the symmetric packed-pair unit of
+//      the all-pairs kernel and the switched pair coefficient; a pair beyond the
+//      cutoff inside a listed tile pair contributes exactly zero;
+//   5. the kick sums, for ion i, the slots of the neighbours of the tile that holds its
+//      sorted position.
+// Nothing is read back to the host, so the step stays one CUDA graph.
+#include <algorithm>
+#include <cmath>
+
+#include "od_device.cuh"
+
+namespace od {
+
+constexpr int CUT_SCAN_PER = 8;                 // elements per thread in the block scan
+constexpr int CUT_SCAN_CHUNK = 1024 * CUT_SCAN_PER;
+
+__device__ __forceinline__ int slab_of(float z, float zoff, float inv_w, int nslab)
+{
+    return min(max((int)((z + zoff) * inv_w), 0), nslab - 1);
+}
+
+// per-warp slab counts: bcount[slab * nblk + warp] (zeroed before)
+__global__ void k_cut_hist(const float4* __restrict__ fpos, int N, float zoff, float inv_w, int nslab, int nblk,
+                           int* __restrict__ bcount)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int key = i < N ? slab_of(fpos[i].z, zoff, inv_w, nslab) : -1;
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    if (key >= 0 && lane == __ffs(peers) - 1) bcount[(long long)key * nblk + (i >> 5)] = __popc(peers);
+}
+
+// exclusive scan of n ints, chunks of CUT_SCAN_CHUNK per 1024-thread block
+__device__ __forceinline__ int block_excl_scan(int v, int* s_w, int& total)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_w[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int t = lane < (int)(blockDim.x >> 5) ? s_w[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        s_w[lane] = t;
+    }
+    __syncthreads();
+    total = s_w[(blockDim.x >> 5) - 1];
+    const int before = w > 0 ? s_w[w - 1] : 0;
+    __syncthreads();
+    return before + x - v;
+}
+
+__global__ void k_cut_scan_chunks(const int* __restrict__ in, int* __restrict__ out, long long n, int* __restrict__ bsum)
+{
+    __shared__ int s_w[32];
+    const long long base = (long long)blockIdx.x * CUT_SCAN_CHUNK + (long long)threadIdx.x * CUT_SCAN_PER;
+    int v[CUT_SCAN_PER], sum = 0;
+#pragma unroll
+    for (int k = 0; k < CUT_SCAN_PER; ++k) {
+        v[k] = base + k < n ? in[base + k] : 0;
+        sum += v[k];
+    }
+    int total;
+    int run = block_excl_scan(sum, s_w, total);
+#pragma unroll
+    for (int k = 0; k < CUT_SCAN_PER; ++k) {
+        if (base + k < n) out[base + k] = run;
+        run += v[k];
+    }
+    if (threadIdx.x == 0) bsum[blockIdx.x] = total;
+}
+
+// exclusive scan of the chunk sums in one block (nb <= 1024 * CUT_SCAN_PER), then added
+__global__ void k_cut_scan_sums(int* __restrict__ bsum, int nb)
+{
+    __shared__ int s_w[32];
+    int v[CUT_SCAN_PER], sum = 0;
+    const int base = threadIdx.x * CUT_SCAN_PER;
+#pragma unroll
+    for (int k = 0; k < CUT_SCAN_PER; ++k) {
+        v[k] = base + k < nb ? bsum[base + k] : 0;
+        sum += v[k];
+    }
+    int total;
+    int run = block_excl_scan(sum, s_w, total);
+#pragma unroll
+    for (int k = 0; k < CUT_SCAN_PER; ++k) {
+        if (base + k < nb) bsum[base + k] = run;
+        run += v[k];
+    }
+}
+
+__global__ void k_cut_scan_add(int* __restrict__ out, long long n, const int* __restrict__ bsum)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] += bsum[i / CUT_SCAN_CHUNK];
+}
+
+// stable scatter into slab order: perm[pos] = i, rank[i] = pos, fsort[pos] = fpos[i]
+__global__ void k_cut_scatter(const float4* __restrict__ fpos, int N, float zoff, float inv_w, int nslab, int nblk,
+                              const int* __restrict__ boff, int* __restrict__ perm, int* __restrict__ rank,
+                              float4* __restrict__ fsort)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const float4 p = i < N ? fpos[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const int key = i < N ? slab_of(p.z, zoff, inv_w, nslab) : -1;
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    if (key < 0) return;
+    const int pos = boff[(long long)key * nblk + (i >> 5)] + __popc(peers & ((1u << lane) - 1u));
+    perm[pos] = i;
+    rank[i] = pos;
+    fsort[pos] = p;
+}
+
+// far-away dummies after the sorted ions (never within the cutoff of anything)
+__global__ void k_cut_dummies(float4* __restrict__ fsort, int N, int n_pad)
+{
+    const int i = N + blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_pad) return;
+    const float far = 3.0e4f + 7.0f * (float)(i - N);
+    fsort[i] = make_float4(far, far, far, 0.0f);
+}
+
+// bounding box of the real ions of each tile (w = 1 if the tile holds any)
+__global__ void k_cut_boxes(const float4* __restrict__ fsort, int N, int TI, float4* __restrict__ lo,
+                            float4* __restrict__ hi)
+{
+    __shared__ float s[6][32];
+    const int t = blockIdx.x;
+    const int q0 = t * TI, q1 = min(N, q0 + TI);
+    float mn[3] = {3e38f, 3e38f, 3e38f}, mx[3] = {-3e38f, -3e38f, -3e38f};
+    for (int q = q0 + (int)threadIdx.x; q < q1; q += blockDim.x) {
+        const float4 p = fsort[q];
+        mn[0] = fminf(mn[0], p.x), mn[1] = fminf(mn[1], p.y), mn[2] = fminf(mn[2], p.z);
+        mx[0] = fmaxf(mx[0], p.x), mx[1] = fmaxf(mx[1], p.y), mx[2] = fmaxf(mx[2], p.z);
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            mn[c] = fminf(mn[c], __shfl_xor_sync(0xffffffffu, mn[c], o));
+            mx[c] = fmaxf(mx[c], __shfl_xor_sync(0xffffffffu, mx[c], o));
+        }
+    if (lane == 0)
+        for (int c = 0; c < 3; ++c) s[c][w] = mn[c], s[3 + c][w] = mx[c];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int ww = 1; ww < (int)(blockDim.x >> 5); ++ww)
+            for (int c = 0; c < 3; ++c) s[c][0] = fminf(s[c][0], s[c][ww]), s[3 + c][0] = fmaxf(s[3 + c][0], s[3 + c][ww]);
+        const float any = q1 > q0 ? 1.f : 0.f;
+        lo[t] = make_float4(s[0][0], s[1][0], s[2][0], any);
+        hi[t] = make_float4(s[3][0], s[4][0], s[5][0], any);
+    }
+}
+
+__device__ __forceinline__ bool tiles_meet(float4 la, float4 ha, float4 lb, float4 hb, float rc2)
+{
+    if (la.w == 0.f || lb.w == 0.f) return false;
+    const float gx = fmaxf(0.f, fmaxf(lb.x - ha.x, la.x - hb.x));
+    const float gy = fmaxf(0.f, fmaxf(lb.y - ha.y, la.y - hb.y));
+    const float gz = fmaxf(0.f, fmaxf(lb.z - ha.z, la.z - hb.z));
+    return fmaf(gx, gx, fmaf(gy, gy, gz * gz)) < rc2;
+}
+
+// neighbour lists (CSR, ascending) and tile pairs (I, J >= I) of the tiles whose boxes
+// come closer than the cutoff, with the slot each side of a pair writes (the position of
+// the other tile in its list); one CTA of 1024 threads, T <= CUT_MAX_TILES.  A tile with
+// more neighbours than max_deg slots empties the lists (no pair is evaluated, the kick
+// reads nothing) and raises ERR_CUTCAP: the step reports the error instead of writing
+// past the slots.
+__global__ void __launch_bounds__(1024) k_cut_lists(const float4* __restrict__ lo, const float4* __restrict__ hi,
+                                                    int T, float rc2, int max_deg, int* __restrict__ nbr_start,
+                                                    int* __restrict__ nbr, int4* __restrict__ units,
+                                                    int* __restrict__ n_units, int* __restrict__ err)
+{
+    __shared__ int s_n[CUT_MAX_TILES + 1], s_u[CUT_MAX_TILES + 1];
+    __shared__ int s_over;
+    if (threadIdx.x == 0) s_over = 0;
+    __syncthreads();
+    for (int I = threadIdx.x; I < T; I += blockDim.x) {
+        const float4 la = lo[I], ha = hi[I];
+        int n = 0, nu = 0;
+        for (int J = 0; J < T; ++J)
+            if (tiles_meet(la, ha, lo[J], hi[J], rc2)) {
+                ++n;
+                nu += J >= I;
+            }
+        s_n[I] = n;
+        s_u[I] = nu;
+        if (n > max_deg) s_over = 1;
+    }
+    __syncthreads();
+    if (s_over) {
+        for (int I = threadIdx.x; I <= T; I += blockDim.x) nbr_start[I] = 0;
+        if (threadIdx.x == 0) {
+            *n_units = 0;
+            atomicOr(err, ERR_CUTCAP);
+        }
+        return;
+    }
+    if (threadIdx.x == 0) {
+        int a = 0, c = 0;
+        for (int I = 0; I < T; ++I) {
+            const int n = s_n[I], nu = s_u[I];
+            s_n[I] = a;
+            s_u[I] = c;
+            a += n;
+            c += nu;
+        }
+        s_n[T] = a;
+        s_u[T] = c;
+        nbr_start[T] = a;
+        *n_units = c;
+    }
+    __syncthreads();
+    for (int I = threadIdx.x; I < T; I += blockDim.x) {
+        const float4 la = lo[I], ha = hi[I];
+        int k = s_n[I];
+        nbr_start[I] = k;
+        for (int J = 0; J < T; ++J)
+            if (tiles_meet(la, ha, lo[J], hi[J], rc2)) nbr[k++] = J;
+    }
+    __syncthreads();
+    // tile pairs with their slots: J's position in I's list is known while walking it;
+    // I's position in J's list by binary search (the lists are ascending)
+    for (int I = threadIdx.x; I < T; I += blockDim.x) {
+        const int k0 = s_n[I], k1 = s_n[I + 1];
+        int ku = s_u[I];
+        for (int k = k0; k < k1; ++k) {
+            const int J = nbr[k];
+            if (J < I) continue;
+            int a = s_n[J], c = s_n[J + 1];
+            while (a < c) {
+                const int m = (a + c) >> 1;
+                if (nbr[m] < I) a = m + 1;
+                else c = m;
+            }
+            units[ku++] = make_int4(I, J, k - k0, a - s_n[J]);
+        }
+    }
+}
+
+// persistent CTAs over the listed tile pairs (their number is read on the device)
+template <int BT, int IPT>
+__global__ void __launch_bounds__(BT) k_forces_cut(const float4* __restrict__ fsort, float4* __restrict__ part,
+                                                   ForceArgs F, const int4* __restrict__ units,
+                                                   const int* __restrict__ n_units)
+{
+    __shared__ float s_acc[2][3][BT / 32][SYM_SUB];
+    __shared__ float4 sj[BT];
+    const long long U = *n_units;
+    long long u = (long long)blockIdx.x * U / gridDim.x;
+    const long long u_end = (long long)(blockIdx.x + 1) * U / gridDim.x;
+    for (; u < u_end; ++u) {
+        const int4 t = units[u];  // (I, J, slot of J in I's list, slot of I in J's list)
+        sym2_unit<BT, IPT, true>(fsort, part, F, t.x, t.y, s_acc, sj, t.z, t.w);
+    }
+}
+
+static int ckc(cudaError_t e) { return e == cudaSuccess ? 0 : (int)e; }
+
+int cut_blocks_per_sm(int ipt)
+{
+    int nb = 0;
+    const void* fn = ipt == 4 ? (const void*)k_forces_cut<256, 4> : (const void*)k_forces_cut<256, 2>;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, 256, 0) != cudaSuccess) return 1;
+    return nb > 0 ? nb : 1;
+}
+
+int launch_cut_dummies(const CutBufs& C, int N, int n_pad, cudaStream_t s)
+{
+    if (n_pad > N) k_cut_dummies<<<(n_pad - N + 255) / 256, 256, 0, s>>>(C.fsort, N, n_pad);
+    return ckc(cudaGetLastError());
+}
+
+int launch_forces_cut(const Phys& P, const Bufs& B, const ForceArgs& F, const CutBufs& C, int grid, cudaStream_t s)
+{
+    const int N = P.N;
+    if (N == 0 || (P.flags & OD_F_NO_IONION)) return 0;
+    const int nblk = (N + 31) / 32;
+    const long long M = (long long)C.nslab * nblk;
+    int rc;
+    if ((rc = ckc(cudaMemsetAsync(C.bcount, 0, sizeof(int) * M, s)))) return rc;
+    const int nthreads = nblk * 32;
+    k_cut_hist<<<(nthreads + 255) / 256, 256, 0, s>>>(B.fpos, N, C.zoff, C.inv_w, C.nslab, nblk, C.bcount);
+    const int nchunk = (int)((M + CUT_SCAN_CHUNK - 1) / CUT_SCAN_CHUNK);
+    k_cut_scan_chunks<<<nchunk, 1024, 0, s>>>(C.bcount, C.boff, M, C.bsum);
+    k_cut_scan_sums<<<1, 1024, 0, s>>>(C.bsum, nchunk);
+    k_cut_scan_add<<<(int)((M + 255) / 256), 256, 0, s>>>(C.boff, M, C.bsum);
+    k_cut_scatter<<<(nthreads + 255) / 256, 256, 0, s>>>(B.fpos, N, C.zoff, C.inv_w, C.nslab, nblk, C.boff, C.perm,
+                                                        C.rank, C.fsort);
+    // the padding after the sorted ions (its length changes with N)
+    if (F.n_pad > N) k_cut_dummies<<<(F.n_pad - N + 255) / 256, 256, 0, s>>>(C.fsort, N, F.n_pad);
+    const int T = F.n_pad / F.TI;
+    k_cut_boxes<<<T, 256, 0, s>>>(C.fsort, N, F.TI, C.box_lo, C.box_hi);
+    k_cut_lists<<<1, 1024, 0, s>>>(C.box_lo, C.box_hi, T, C.rc2_tile, C.max_deg, C.nbr_start, C.nbr, C.units,
+                                   C.n_units, C.err);
+    if (F.TI == 1024)
+        k_forces_cut<256, 4><<<grid, 256, 0, s>>>(C.fsort, B.part, F, C.units, C.n_units);
+    else
+        k_forces_cut<256, 2><<<grid, 256, 0, s>>>(C.fsort, B.part, F, C.units, C.n_units);
+    return ckc(cudaGetLastError());
+}
+
+}  // namespace od

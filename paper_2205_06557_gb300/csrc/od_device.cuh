@@ -440,12 +440,41 @@ __device__ __forceinline__ float pair_c3(float dx, float dy, float dz)
     return (e * (ri * ri)) * (ri + LN2);
 }
 
+// pair_c3 with the ion-ion cutoff (Sec. 5; the switching form is a reading): the pair
+// energy is multiplied by S(x) = 1 - 10 x^3 + 15 x^4 - 6 x^5, x = (s - s0) w_inv clamped to
+// [0, 1], and the force is minus the gradient of the switched energy.  In the scaled
+// units of pair_c3 this is c3 = e ri^2 [(ri + ln2) S(x) - S'(x) w_inv], with
+// S'(x) = -30 x^2 (1 - x)^2.  The clamp makes it exactly the plain term for s <= s0 and
+// exactly 0 from the cutoff on (S(1) = S'(1) = 0); there is no branch.
+__device__ __forceinline__ float switch_bracket(float s, float ri, float s0, float w_inv)
+{
+    constexpr float LN2 = 0.69314718055994531f;
+    const float x = fminf(fmaxf((s - s0) * w_inv, 0.f), 1.f);
+    const float x2 = x * x, y = 1.f - x;
+    const float S = fmaf(-(x2 * x), fmaf(fmaf(6.f, x, -15.f), x, 10.f), 1.f);
+    const float dS = -30.f * x2 * (y * y);
+    return fmaf(ri + LN2, S, -dS * w_inv);
+}
+
+__device__ __forceinline__ float pair_c3_cut(float dx, float dy, float dz, float s0, float w_inv)
+{
+    constexpr float EPS2 = 1e-24f;
+    float r2 = fmaf(dx, dx, EPS2);
+    r2 = fmaf(dy, dy, r2);
+    r2 = fmaf(dz, dz, r2);
+    const float ri = rsqrt_approx(r2);
+    const float s = r2 * ri;
+    const float e = ex2_approx(-s);
+    return (e * (ri * ri)) * switch_bracket(s, ri, s0, w_inv);
+}
+
 // Accumulate into IPT targets per thread the pair terms of sources [j0, j1), staged
-// through shared memory BT at a time (acc += d c3, c3 from pair_c3).
-template <int BT, int IPT>
+// through shared memory BT at a time (acc += d c3, c3 from pair_c3, or from pair_c3_cut
+// with the switching zone s0, w_inv when CUT).
+template <int BT, int IPT, bool CUT = false>
 __device__ __forceinline__ void pair_chunk(const float4* __restrict__ fpos, int j0, int j1, const float* xi,
                                            const float* yi, const float* zi, float* ax, float* ay, float* az,
-                                           float4* sj)
+                                           float4* sj, float s0 = 0.f, float w_inv = 0.f)
 {
     for (int jb = j0; jb < j1; jb += BT) {
         __syncthreads();
@@ -463,7 +492,7 @@ __device__ __forceinline__ void pair_chunk(const float4* __restrict__ fpos, int 
 #pragma unroll
             for (int k = 0; k < IPT; ++k) {
                 const float dx = pj.x - xi[k], dy = pj.y - yi[k], dz = pj.z - zi[k];
-                const float c3 = pair_c3(dx, dy, dz);
+                const float c3 = CUT ? pair_c3_cut(dx, dy, dz, s0, w_inv) : pair_c3(dx, dy, dz);
                 bx[k] = fmaf(c3, dx, bx[k]);
                 by[k] = fmaf(c3, dy, by[k]);
                 bz[k] = fmaf(c3, dz, bz[k]);
@@ -688,6 +717,25 @@ __device__ __forceinline__ f32x2 pair_c3x2(f32x2 dx, f32x2 dy, f32x2 dz)
     return mul2(mul2(e, mul2(ri, ri)), add2(ri, ln2));
 }
 
+// pair_c3_cut for two pairs at once: the packed plain coefficient's steps, then the
+// switching bracket per lane
+__device__ __forceinline__ f32x2 pair_c3x2_cut(f32x2 dx, f32x2 dy, f32x2 dz, float s0, float w_inv)
+{
+    const f32x2 eps2 = pk2(1e-24f, 1e-24f);
+    f32x2 r2 = fma2(dx, dx, eps2);
+    r2 = fma2(dy, dy, r2);
+    r2 = fma2(dz, dz, r2);
+    float ra, rb;
+    upk2(r2, ra, rb);
+    const float ria = rsqrt_approx(ra), rib = rsqrt_approx(rb);
+    const f32x2 ri = pk2(ria, rib);
+    float sa, sb;
+    upk2(mul2(r2, ri), sa, sb);
+    const f32x2 e = pk2(ex2_approx(-sa), ex2_approx(-sb));
+    const f32x2 br = pk2(switch_bracket(sa, ria, s0, w_inv), switch_bracket(sb, rib, s0, w_inv));
+    return mul2(mul2(e, mul2(ri, ri)), br);
+}
+
 constexpr int SYM_SUB = 128;  // sources per combine step of the symmetric kernels
 
 // One tile-pair unit (I, J >= I) of the symmetric kernel with packed FP32 pairs: the same
@@ -698,10 +746,13 @@ constexpr int SYM_SUB = 128;  // sources per combine step of the symmetric kerne
 // with the target-side sign and negated when the warps' sums are combined.  Every unit
 // starts on combine buffer 0 and ends on buffer 1, so consecutive units need no barrier
 // between them beyond the one per combine step.
-template <int BT, int IPT>
+// slot_i / slot_j: the partial slots that receive the sums of the ions of tile I / J (the
+// all-pairs kernels pass J / I; the cutoff passes the positions of J and I in the other
+// tile's neighbour list)
+template <int BT, int IPT, bool CUT = false>
 __device__ __forceinline__ void sym2_unit(const float4* __restrict__ fpos, float4* __restrict__ part,
                                           const ForceArgs& F, int I, int J, float (&s_acc)[2][3][BT / 32][SYM_SUB],
-                                          float4* sj)
+                                          float4* sj, int slot_i, int slot_j)
 {
     constexpr int NW = BT / 32;
     constexpr int TI = BT * IPT;
@@ -720,7 +771,7 @@ __device__ __forceinline__ void sym2_unit(const float4* __restrict__ fpos, float
         az[k] = 0.f;
     }
     if (I == J) {
-        pair_chunk<BT, IPT>(fpos, I * TI, I * TI + TI, xi, yi, zi, ax, ay, az, sj);
+        pair_chunk<BT, IPT, CUT>(fpos, I * TI, I * TI + TI, xi, yi, zi, ax, ay, az, sj, F.cut_s0, F.cut_inv_w);
     } else {
         f32x2 xd[IPT], yd[IPT], zd[IPT], ax2[IPT], ay2[IPT], az2[IPT];
 #pragma unroll
@@ -744,7 +795,7 @@ __device__ __forceinline__ void sym2_unit(const float4* __restrict__ fpos, float
 #pragma unroll
                     for (int k = 0; k < IPT; ++k) {
                         const f32x2 dx = sub2(xj, xd[k]), dy = sub2(yj, yd[k]), dz = sub2(zj, zd[k]);
-                        const f32x2 c3 = pair_c3x2(dx, dy, dz);
+                        const f32x2 c3 = CUT ? pair_c3x2_cut(dx, dy, dz, F.cut_s0, F.cut_inv_w) : pair_c3x2(dx, dy, dz);
                         ax2[k] = fma2(c3, dx, ax2[k]);
                         ay2[k] = fma2(c3, dy, ay2[k]);
                         az2[k] = fma2(c3, dz, az2[k]);
@@ -781,7 +832,7 @@ __device__ __forceinline__ void sym2_unit(const float4* __restrict__ fpos, float
                     sy += s_acc[buf][1][ww][j];
                     sz += s_acc[buf][2][ww][j];
                 }
-                part[(long long)I * F.n_pad + jb + sc * SYM_SUB + j] = make_float4(-sx, -sy, -sz, 0.f);
+                part[(long long)slot_j * F.n_pad + jb + sc * SYM_SUB + j] = make_float4(-sx, -sy, -sz, 0.f);
             }
         }
 #pragma unroll
@@ -795,7 +846,7 @@ __device__ __forceinline__ void sym2_unit(const float4* __restrict__ fpos, float
             az[k] = l0 + h0;
         }
     }
-    float4* out = part + (long long)J * F.n_pad + I * TI + threadIdx.x;
+    float4* out = part + (long long)slot_i * F.n_pad + I * TI + threadIdx.x;
 #pragma unroll
     for (int k = 0; k < IPT; ++k) out[k * BT] = make_float4(ax[k], ay[k], az[k], 0.f);
 }
@@ -813,7 +864,7 @@ __global__ void __launch_bounds__(BT) k_forces_sym2(const float4* __restrict__ f
     int I, J;
     tri_unit(u, F.JS, I, J);
     for (; u < u_end; ++u) {
-        sym2_unit<BT, IPT>(fpos, part, F, I, J, s_acc, sj);
+        sym2_unit<BT, IPT>(fpos, part, F, I, J, s_acc, sj, J, I);
         if (++J == F.JS) J = ++I;
     }
 }
@@ -876,10 +927,16 @@ __device__ __forceinline__ void kick_body(const Phys& P, const Bufs& B, const Fo
         z = X[2 * cap + i];
         float ax = 0.f, ay = 0.f, az = 0.f;
         if (!(P.flags & OD_F_NO_IONION)) {
-            // slots of this ion: the blocks that covered its tile (ordered-pair kernel) or
-            // one per tile (symmetric kernel)
+            // slots of this ion: the blocks that covered its tile (ordered-pair kernel), one
+            // per tile (symmetric kernel) or one per neighbour of the tile that holds its
+            // sorted position (cutoff: slots 0 .. degree - 1)
             int ns = F.W;
-            if (!F.sym) {
+            int q = i;  // position in the pair kernel's ion order
+            if (F.cut) {
+                q = F.rank[i];
+                const int t = q / F.TI;
+                ns = F.nbr_start[t + 1] - F.nbr_start[t];
+            } else if (!F.sym) {
                 const int t = i / F.TI;
                 const long long u0 = (long long)t * F.JS;
                 ns = owner_of(u0 + F.JS - 1, F.U, F.G) - owner_of(u0, F.U, F.G) + 1;
@@ -890,7 +947,7 @@ __device__ __forceinline__ void kick_body(const Phys& P, const Bufs& B, const Fo
                 float bx = 0.f, by = 0.f, bz = 0.f;
 #pragma unroll 8
                 for (int s = s0; s < s1; ++s) {
-                    const float4 p = __ldcs(B.part + (long long)s * F.n_pad + i);
+                    const float4 p = __ldcs(B.part + (long long)s * F.n_pad + q);
                     bx += p.x;
                     by += p.y;
                     bz += p.z;

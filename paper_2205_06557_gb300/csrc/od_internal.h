@@ -19,6 +19,7 @@ constexpr int ERR_NAN = 1;
 constexpr int ERR_TIMEOUT = 2;
 constexpr int ERR_OVERFLOW = 4;
 constexpr int ERR_PLACE = 8;
+constexpr int ERR_CUTCAP = 16;  // cutoff neighbour lists exceed the slot capacity
 constexpr long long SPIN_LIMIT = 1ll << 22;  // ~4 s of polling with the 1 us back-off
 constexpr int VTAB_K = 4096;                  // intervals of the tabulated inverse flux CDFs
 
@@ -118,6 +119,14 @@ struct ForceArgs {
     int W;       // partial slots
     long long U; // units = n_itiles * JS (symmetric: T (T + 1) / 2 tile pairs)
     int sym;     // 1: symmetric kernel, JC = TI, JS = W = T tiles, every ion has T slots
+    // ion-ion cutoff (symmetric tile pairs over z-sorted ions): switching zone in scaled
+    // units [cut_s0, cut_s0 + 1 / cut_inv_w]; ion i sits at rank[i] in the sorted order and
+    // its tile I has nbr_start[I + 1] - nbr_start[I] neighbours, whose sums fill its slots
+    // 0 .. degree - 1 (W = slot capacity)
+    int cut;
+    float cut_s0, cut_inv_w;
+    const int* nbr_start;
+    const int* rank;
 };
 
 // One run of a batched launch (od_batch.cu): its parameters, buffers and pair plan.
@@ -153,8 +162,35 @@ int launch_forces(const Phys& P, const Bufs& B, const ForceArgs& F, int variant,
 int launch_kick(const Phys& P, const Bufs& B, const ForceArgs& F, int mode, cudaStream_t s);
 int launch_dust(const Phys& P, const Bufs& B, int mode, cudaStream_t s);
 int launch_stats(const Phys& P, const Bufs& B, double* mean_se, cudaStream_t s);
+int launch_hist(const Phys& P, const Bufs& B, unsigned long long* counts, int nr, int nz, double inv_dr,
+                double inv_dz, int sms, cudaStream_t s);
 int launch_eout_grid(double R, double H, double lam, int nx, int nz, int nq, const double* gl_x,
                      const double* gl_w, double* out, cudaStream_t s);
+
+// ion-ion cutoff (od_cut.cu): buffers of the slab sort, tile boxes and tile lists;
+// lengths in the pair kernel's scaled units
+constexpr int CUT_MAX_TILES = 4096;
+struct CutBufs {
+    int nslab;
+    float zoff, inv_w, rc2_tile;
+    int* bcount;   // [nslab][warps] slab counts
+    int* boff;     // their exclusive scan
+    int* bsum;     // scan chunk sums
+    int* perm;     // sorted position -> ion
+    int* rank;     // ion -> sorted position
+    float4* fsort; // sorted scaled positions, far dummies after N
+    float4* box_lo;
+    float4* box_hi;
+    int* nbr_start;  // [T + 1]
+    int* nbr;        // [T * T] neighbour tiles, ascending per tile
+    int4* units;     // [T (T + 1) / 2] (I, J >= I, slot of J in I's list, slot of I in J's list)
+    int* n_units;
+    int max_deg;     // slot capacity per ion
+    int* err;        // the run's error word (Ctrl::err)
+};
+int launch_forces_cut(const Phys& P, const Bufs& B, const ForceArgs& F, const CutBufs& C, int grid, cudaStream_t s);
+int launch_cut_dummies(const CutBufs& C, int N, int n_pad, cudaStream_t s);
+int cut_blocks_per_sm(int ipt);
 
 // pair-kernel variants: (threads per block, targets per thread, symmetric)
 struct ForceVariant {

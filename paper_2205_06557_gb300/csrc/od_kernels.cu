@@ -300,6 +300,50 @@ int launch_dust(const Phys& P, const Bufs& B, int mode, cudaStream_t s)
     return ck(cudaGetLastError());
 }
 
+// n(r, z) binning of the ions at the end of a step (observability): bin indices from
+// the FP64 positions with explicitly rounded operations (no contraction), so a host
+// binning that evaluates r = sqrt(x*x + y*y), r * (nr / R) and (z + H/2) * (nz / H)
+// in IEEE FP64 finds the same bins; integer counts, so the result does not depend on the
+// order of the atomics.  Small maps are privatised in shared memory per block.
+constexpr int HIST_SMEM_BINS = 12288;
+
+__global__ void k_hist(Phys P, Bufs B, unsigned long long* counts, int nr, int nz, double inv_dr, double inv_dz)
+{
+    extern __shared__ unsigned s_h[];
+    const int nb = nr * nz;
+    const bool priv = nb <= HIST_SMEM_BINS;
+    if (priv)
+        for (int b = threadIdx.x; b < nb; b += blockDim.x) s_h[b] = 0u;
+    __syncthreads();
+    const long long step = B.ctrl->step;  // positions after step n live in buffer n & 1
+    const double* X = B.x[step & 1];
+    const double hz = 0.5 * P.H;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.N; i += gridDim.x * blockDim.x) {
+        const double x = X[i], y = X[B.cap + i], z = X[2 * B.cap + i];
+        const double r = __dsqrt_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)));
+        const int ir = min(max((int)__dmul_rn(r, inv_dr), 0), nr - 1);
+        const int iz = min(max((int)__dmul_rn(__dadd_rn(z, hz), inv_dz), 0), nz - 1);
+        if (priv) atomicAdd(&s_h[iz * nr + ir], 1u);
+        else atomicAdd(&counts[iz * nr + ir], 1ull);
+    }
+    if (priv) {
+        __syncthreads();
+        for (int b = threadIdx.x; b < nb; b += blockDim.x)
+            if (s_h[b]) atomicAdd(&counts[b], (unsigned long long)s_h[b]);
+    }
+}
+
+int launch_hist(const Phys& P, const Bufs& B, unsigned long long* counts, int nr, int nz, double inv_dr, double inv_dz,
+                int sms, cudaStream_t s)
+{
+    if (P.N == 0) return 0;
+    const int nb = nr * nz;
+    const size_t smem = nb <= HIST_SMEM_BINS ? sizeof(unsigned) * nb : 0;
+    const int grid = std::max(1, std::min((P.N + 255) / 256, 2 * sms));
+    k_hist<<<grid, 256, smem, s>>>(P, B, counts, nr, nz, inv_dr, inv_dz);
+    return ck(cudaGetLastError());
+}
+
 int launch_stats(const Phys& P, const Bufs& B, double* out, cudaStream_t s)
 {
     k_stats<<<1, 128, 0, s>>>(P, B, out);

@@ -68,3 +68,26 @@ def test_null_arguments(L):
     assert L.od_create(None, None) == -1
     assert L.od_step(None, 1) == -1
     L.od_destroy(None)
+
+
+def test_checkpoint_loader_rejects_foreign_files_on_host(L, tmp_path):
+    """od_load checks the file before any device work"""
+    h = ctypes.c_void_p()
+    bad = tmp_path / "not_a_checkpoint.bin"
+    bad.write_bytes(b"hello, this is not a checkpoint" * 10)
+    assert L.od_load(os.fsencode(str(bad)), None, ctypes.byref(h)) == -1
+    assert "checkpoint" in od.od_last_error()
+    trunc = tmp_path / "truncated.bin"
+    trunc.write_bytes(b"ODCKPT01" + b"\x01\x00\x00\x00")
+    assert L.od_load(os.fsencode(str(trunc)), None, ctypes.byref(h)) == -1
+    assert L.od_load(os.fsencode(str(tmp_path / "missing.bin")), None, ctypes.byref(h)) == -1
+    assert not h.value
+
+
+def test_observability_calls_reject_null_handles(L, tmp_path):
+    path = os.fsencode(str(tmp_path / "x.xyz"))
+    assert L.od_save(None, path) == -1
+    assert L.od_write_ions(None, path, 0) == -1
+    assert L.od_density_enable(None, 8, 8) == -1
+    assert L.od_density_read(None, None, None, None) == -1
+    assert L.od_num_dust(None) == -1
