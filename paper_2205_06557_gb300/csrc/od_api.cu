@@ -669,8 +669,8 @@ int ensure_series(od_handle* h, long long need)
 void free_cut(od_handle* h)
 {
     CutBufs& C = h->C;
-    void* ptrs[] = {C.bcount, C.boff, C.bsum, C.perm, C.rank, C.fsort, C.box_lo, C.box_hi,
-                    C.nbr_start, C.nbr, C.units, C.n_units};
+    void* ptrs[] = {C.bcount, C.boff, C.bsum, C.perm, C.rank, C.fsort, C.box_lo, C.box_hi, C.nbr_start,
+                    C.nbr, C.units, C.n_units, C.cnt, C.ucnt, C.ustart, C.over};
     for (void* q : ptrs) cudaFree(q);
     C = CutBufs{};
 }
@@ -1047,11 +1047,11 @@ int od_set_cutoff(od_handle* h, double r_cut, double r_switch)
     const int T = (int)(npad_max / TI);
     if (T > CUT_MAX_TILES)
         return fail(h, OD_EINVAL, "cutoff: at most " + std::to_string(CUT_MAX_TILES * TI) + " ions");
-    // slabs of about an eighth of the cutoff (at most 256; the slab-by-warp count matrix
-    // stays below 64M entries)
+    // slabs of about an eighth of the cutoff (the slab-by-warp count matrix stays below
+    // 64M entries)
     const long long nblk = (h->cap + 31) / 32;
-    int nslab = (int)std::min(256.0, std::max(1.0, std::ceil(h->P.H / (r_cut / 8.0))));
-    while ((long long)nslab * nblk > (64ll << 20) && nslab > 1) nslab /= 2;
+    int nslab = (int)std::min(65536.0, std::max(1.0, std::ceil(h->P.H / (r_cut / 8.0))));
+    while ((long long)nslab * nblk > (64ll << 20) && nslab > 1) nslab = (nslab + 1) / 2;
     const double w = h->P.H / nslab;
     // slot capacity: the tiles within the cutoff plus two tile extents, for a uniform
     // density, with a margin of half again
@@ -1070,6 +1070,8 @@ int od_set_cutoff(od_handle* h, double r_cut, double r_switch)
     C.inv_w = (float)(1.0 / (w * ls));
     const double rcs = r_cut * ls * (1.0 + 1e-5);  // box test: never drop a pair inside the cutoff
     C.rc2_tile = (float)(rcs * rcs);
+    const double rss = r_switch * ls * (1.0 - 1e-5);  // plain units: never skip a switched pair
+    C.rs2_tile = (float)(rss * rss);
     C.max_deg = max_deg;
     C.err = (int*)((char*)h->B.ctrl + offsetof(Ctrl, err));
     const long long M = (long long)nslab * nblk;
@@ -1086,6 +1088,10 @@ int od_set_cutoff(od_handle* h, double r_cut, double r_switch)
     OD_CK(h, cudaMalloc(&C.nbr, sizeof(int) * (size_t)T * T));
     OD_CK(h, cudaMalloc(&C.units, sizeof(int4) * ((size_t)T * (T + 1) / 2)));
     OD_CK(h, cudaMalloc(&C.n_units, sizeof(int)));
+    OD_CK(h, cudaMalloc(&C.cnt, sizeof(int) * T));
+    OD_CK(h, cudaMalloc(&C.ucnt, sizeof(int) * T));
+    OD_CK(h, cudaMalloc(&C.ustart, sizeof(int) * T));
+    OD_CK(h, cudaMalloc(&C.over, sizeof(int)));
     h->cut_on = true;
     h->r_cut = r_cut;
     h->r_switch = r_switch;

@@ -8,11 +8,12 @@
 //      inside a slab is the ion order (deterministic);
 //   2. the sorted positions are cut into tiles of TI ions; each tile gets the bounding
 //      box of its ions;
-//   3. one CTA lists, for every tile, the tiles whose boxes come closer than the
-//      cutoff (neighbour lists, CSR) and the tile pairs (I, J >= I) among them;
+//   3. warps list, for every tile, the tiles whose boxes come closer than the cutoff
+//      (neighbour lists, CSR) and the tile pairs (I, J >= I) among them;
 //   4. persistent CTAs evaluate those tile pairs with the symmetric packed-pair unit of
-//      the all-pairs kernel and the switched pair coefficient; a pair beyond the
-//      cutoff inside a listed tile pair contributes exactly zero;
+//      the all-pairs kernel and the switched pair coefficient (the plain one where the
+//      two boxes lie wholly inside the switching distance); a pair beyond the cutoff
+//      inside a listed tile pair contributes exactly zero;
 //   5. the kick sums, for ion i, the slots of the neighbours of the tile that holds its
 //      sorted position.
 // Nothing is read back to the host, so the step stays one CUDA graph.
@@ -184,81 +185,134 @@ __device__ __forceinline__ bool tiles_meet(float4 la, float4 ha, float4 lb, floa
     return fmaf(gx, gx, fmaf(gy, gy, gz * gz)) < rc2;
 }
 
-// neighbour lists (CSR, ascending) and tile pairs (I, J >= I) of the tiles whose boxes
-// come closer than the cutoff, with the slot each side of a pair writes (the position of
-// the other tile in its list); one CTA of 1024 threads, T <= CUT_MAX_TILES.  A tile with
-// more neighbours than max_deg slots empties the lists (no pair is evaluated, the kick
-// reads nothing) and raises ERR_CUTCAP: the step reports the error instead of writing
-// past the slots.
-__global__ void __launch_bounds__(1024) k_cut_lists(const float4* __restrict__ lo, const float4* __restrict__ hi,
-                                                    int T, float rc2, int max_deg, int* __restrict__ nbr_start,
-                                                    int* __restrict__ nbr, int4* __restrict__ units,
-                                                    int* __restrict__ n_units, int* __restrict__ err)
+constexpr int CUT_PLAIN = 1 << 30;  // unit flag: every pair inside the switching distance
+
+// farthest distance^2 between two boxes: below the switching distance every pair of the
+// two tiles has S = 1 and S' = 0, and the plain coefficient gives the same bits
+__device__ __forceinline__ float boxes_far2(float4 la, float4 ha, float4 lb, float4 hb)
 {
-    __shared__ int s_n[CUT_MAX_TILES + 1], s_u[CUT_MAX_TILES + 1];
+    const float fx = fmaxf(hb.x - la.x, ha.x - lb.x), fy = fmaxf(hb.y - la.y, ha.y - lb.y);
+    const float fz = fmaxf(hb.z - la.z, ha.z - lb.z);
+    return fmaf(fx, fx, fmaf(fy, fy, fz * fz));
+}
+
+// Neighbour lists (CSR, ascending) and tile pairs (I, J >= I) of the tiles whose boxes
+// come closer than the cutoff, with the slot each side of a pair writes (the position of
+// the other tile in its list).  One warp per tile in every pass; T <= CUT_MAX_TILES.
+// A tile with more neighbours than max_deg slots empties the lists (no pair is
+// evaluated, the kick reads nothing) and raises ERR_CUTCAP: the step reports the error
+// instead of writing past the slots.
+
+// pass 1: neighbours and tile pairs (J >= I) per tile
+__global__ void k_cut_count(const float4* __restrict__ lo, const float4* __restrict__ hi, int T, float rc2,
+                            int* __restrict__ cnt, int* __restrict__ ucnt)
+{
+    const int I = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (I >= T) return;
+    const float4 la = lo[I], ha = hi[I];
+    int n = 0, nu = 0;
+    for (int J = lane; J < T; J += 32)
+        if (tiles_meet(la, ha, lo[J], hi[J], rc2)) {
+            ++n;
+            nu += J >= I;
+        }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        n += __shfl_xor_sync(0xffffffffu, n, o);
+        nu += __shfl_xor_sync(0xffffffffu, nu, o);
+    }
+    if (lane == 0) {
+        cnt[I] = n;
+        ucnt[I] = nu;
+    }
+}
+
+// pass 2 (one CTA of 1024): exclusive scans, list starts, unit starts and count, overflow
+__global__ void __launch_bounds__(1024) k_cut_offsets(const int* __restrict__ cnt, const int* __restrict__ ucnt, int T,
+                                                      int max_deg, int* __restrict__ nbr_start,
+                                                      int* __restrict__ ustart, int* __restrict__ n_units,
+                                                      int* __restrict__ over, int* __restrict__ err)
+{
+    __shared__ int s_w[32];
     __shared__ int s_over;
     if (threadIdx.x == 0) s_over = 0;
     __syncthreads();
-    for (int I = threadIdx.x; I < T; I += blockDim.x) {
-        const float4 la = lo[I], ha = hi[I];
-        int n = 0, nu = 0;
-        for (int J = 0; J < T; ++J)
-            if (tiles_meet(la, ha, lo[J], hi[J], rc2)) {
-                ++n;
-                nu += J >= I;
-            }
-        s_n[I] = n;
-        s_u[I] = nu;
-        if (n > max_deg) s_over = 1;
+    constexpr int PER = CUT_MAX_TILES / 1024;
+    const int base = threadIdx.x * PER;
+    int v[PER], u[PER], sv = 0, su = 0;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        v[k] = base + k < T ? cnt[base + k] : 0;
+        u[k] = base + k < T ? ucnt[base + k] : 0;
+        if (v[k] > max_deg) s_over = 1;
+        sv += v[k];
+        su += u[k];
     }
-    __syncthreads();
-    if (s_over) {
-        for (int I = threadIdx.x; I <= T; I += blockDim.x) nbr_start[I] = 0;
-        if (threadIdx.x == 0) {
-            *n_units = 0;
-            atomicOr(err, ERR_CUTCAP);
+    int tv, tu;
+    int rv = block_excl_scan(sv, s_w, tv);
+    int ru = block_excl_scan(su, s_w, tu);
+    const bool ov = s_over != 0;
+#pragma unroll
+    for (int k = 0; k < PER; ++k)
+        if (base + k < T) {
+            nbr_start[base + k] = ov ? 0 : rv;
+            ustart[base + k] = ru;
+            rv += v[k];
+            ru += u[k];
         }
-        return;
-    }
     if (threadIdx.x == 0) {
-        int a = 0, c = 0;
-        for (int I = 0; I < T; ++I) {
-            const int n = s_n[I], nu = s_u[I];
-            s_n[I] = a;
-            s_u[I] = c;
-            a += n;
-            c += nu;
-        }
-        s_n[T] = a;
-        s_u[T] = c;
-        nbr_start[T] = a;
-        *n_units = c;
+        nbr_start[T] = ov ? 0 : tv;
+        *n_units = ov ? 0 : tu;
+        *over = ov ? 1 : 0;
+        if (ov) atomicOr(err, ERR_CUTCAP);
     }
-    __syncthreads();
-    for (int I = threadIdx.x; I < T; I += blockDim.x) {
-        const float4 la = lo[I], ha = hi[I];
-        int k = s_n[I];
-        nbr_start[I] = k;
-        for (int J = 0; J < T; ++J)
-            if (tiles_meet(la, ha, lo[J], hi[J], rc2)) nbr[k++] = J;
+}
+
+// pass 3: the neighbour lists in ascending order (ballot prefix per group of 32)
+__global__ void k_cut_fill(const float4* __restrict__ lo, const float4* __restrict__ hi, int T, float rc2,
+                           const int* __restrict__ nbr_start, const int* __restrict__ over, int* __restrict__ nbr)
+{
+    const int I = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (I >= T || *over) return;
+    const float4 la = lo[I], ha = hi[I];
+    int k = nbr_start[I];
+    for (int J0 = 0; J0 < T; J0 += 32) {
+        const int J = J0 + lane;
+        const bool m = J < T && tiles_meet(la, ha, lo[J], hi[J], rc2);
+        const unsigned mask = __ballot_sync(0xffffffffu, m);
+        if (m) nbr[k + __popc(mask & ((1u << lane) - 1u))] = J;
+        k += __popc(mask);
     }
-    __syncthreads();
-    // tile pairs with their slots: J's position in I's list is known while walking it;
-    // I's position in J's list by binary search (the lists are ascending)
-    for (int I = threadIdx.x; I < T; I += blockDim.x) {
-        const int k0 = s_n[I], k1 = s_n[I + 1];
-        int ku = s_u[I];
-        for (int k = k0; k < k1; ++k) {
-            const int J = nbr[k];
-            if (J < I) continue;
-            int a = s_n[J], c = s_n[J + 1];
+}
+
+// pass 4: tile pairs (I, J >= I) with their slots: J's position in I's list, I's position
+// in J's list by binary search (ascending), and the plain flag
+__global__ void k_cut_units(const float4* __restrict__ lo, const float4* __restrict__ hi, int T, float rs2,
+                            const int* __restrict__ nbr_start, const int* __restrict__ nbr,
+                            const int* __restrict__ ustart, const int* __restrict__ over, int4* __restrict__ units)
+{
+    const int I = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (I >= T || *over) return;
+    const int k0 = nbr_start[I], k1 = nbr_start[I + 1];
+    const float4 la = lo[I], ha = hi[I];
+    int ku = ustart[I];
+    for (int kb = k0; kb < k1; kb += 32) {
+        const int k = kb + lane;
+        const int J = k < k1 ? nbr[k] : -1;
+        const bool m = J >= I;
+        const unsigned mask = __ballot_sync(0xffffffffu, m);
+        if (m) {
+            int a = nbr_start[J], c = nbr_start[J + 1];
             while (a < c) {
-                const int m = (a + c) >> 1;
-                if (nbr[m] < I) a = m + 1;
-                else c = m;
+                const int mid = (a + c) >> 1;
+                if (nbr[mid] < I) a = mid + 1;
+                else c = mid;
             }
-            units[ku++] = make_int4(I, J, k - k0, a - s_n[J]);
+            const bool plain = boxes_far2(la, ha, lo[J], hi[J]) < rs2;
+            units[ku + __popc(mask & ((1u << lane) - 1u))] =
+                make_int4(I, J, k - k0, (a - nbr_start[J]) | (plain ? CUT_PLAIN : 0));
         }
+        ku += __popc(mask);
     }
 }
 
@@ -274,8 +328,11 @@ __global__ void __launch_bounds__(BT) k_forces_cut(const float4* __restrict__ fs
     long long u = (long long)blockIdx.x * U / gridDim.x;
     const long long u_end = (long long)(blockIdx.x + 1) * U / gridDim.x;
     for (; u < u_end; ++u) {
-        const int4 t = units[u];  // (I, J, slot of J in I's list, slot of I in J's list)
-        sym2_unit<BT, IPT, true>(fsort, part, F, t.x, t.y, s_acc, sj, t.z, t.w);
+        const int4 t = units[u];  // (I, J, slot of J in I's list, slot of I in J's list | flag)
+        if (t.w & CUT_PLAIN)
+            sym2_unit<BT, IPT, false>(fsort, part, F, t.x, t.y, s_acc, sj, t.z, t.w & (CUT_PLAIN - 1));
+        else
+            sym2_unit<BT, IPT, true>(fsort, part, F, t.x, t.y, s_acc, sj, t.z, t.w);
     }
 }
 
@@ -315,8 +372,11 @@ int launch_forces_cut(const Phys& P, const Bufs& B, const ForceArgs& F, const Cu
     if (F.n_pad > N) k_cut_dummies<<<(F.n_pad - N + 255) / 256, 256, 0, s>>>(C.fsort, N, F.n_pad);
     const int T = F.n_pad / F.TI;
     k_cut_boxes<<<T, 256, 0, s>>>(C.fsort, N, F.TI, C.box_lo, C.box_hi);
-    k_cut_lists<<<1, 1024, 0, s>>>(C.box_lo, C.box_hi, T, C.rc2_tile, C.max_deg, C.nbr_start, C.nbr, C.units,
-                                   C.n_units, C.err);
+    const int wb = (T + 7) / 8;  // 8 warps per CTA, one per tile
+    k_cut_count<<<wb, 256, 0, s>>>(C.box_lo, C.box_hi, T, C.rc2_tile, C.cnt, C.ucnt);
+    k_cut_offsets<<<1, 1024, 0, s>>>(C.cnt, C.ucnt, T, C.max_deg, C.nbr_start, C.ustart, C.n_units, C.over, C.err);
+    k_cut_fill<<<wb, 256, 0, s>>>(C.box_lo, C.box_hi, T, C.rc2_tile, C.nbr_start, C.over, C.nbr);
+    k_cut_units<<<wb, 256, 0, s>>>(C.box_lo, C.box_hi, T, C.rs2_tile, C.nbr_start, C.nbr, C.ustart, C.over, C.units);
     if (F.TI == 1024)
         k_forces_cut<256, 4><<<grid, 256, 0, s>>>(C.fsort, B.part, F, C.units, C.n_units);
     else

@@ -172,7 +172,7 @@ int launch_eout_grid(double R, double H, double lam, int nx, int nz, int nq, con
 constexpr int CUT_MAX_TILES = 4096;
 struct CutBufs {
     int nslab;
-    float zoff, inv_w, rc2_tile;
+    float zoff, inv_w, rc2_tile, rs2_tile;
     int* bcount;   // [nslab][warps] slab counts
     int* boff;     // their exclusive scan
     int* bsum;     // scan chunk sums
@@ -185,6 +185,10 @@ struct CutBufs {
     int* nbr;        // [T * T] neighbour tiles, ascending per tile
     int4* units;     // [T (T + 1) / 2] (I, J >= I, slot of J in I's list, slot of I in J's list)
     int* n_units;
+    int* cnt;        // [T] neighbours per tile
+    int* ucnt;       // [T] tile pairs (J >= I) per tile
+    int* ustart;     // [T] first unit of each tile
+    int* over;       // 1: the lists exceed max_deg
     int max_deg;     // slot capacity per ion
     int* err;        // the run's error word (Ctrl::err)
 };
