@@ -247,7 +247,8 @@ def run_ours(args):
     t_max, pairs = job_totals(dist, t_ms, float(N) * (N - 1) * args.steps, "cuda")
     value = pairs / (t_max / 1e3)
 
-    # end to end through the ABI with host buffers: upload state, one step, read back
+    # end to end through the ABI with page-locked host buffers: upload state, one step,
+    # read the state and the grain results back
     x, v, a, ids = run.get_ions()
     pin = lambda arr: torch.from_numpy(np.ascontiguousarray(arr)).pin_memory().numpy()
     hx, hv, ha, hid = pin(x), pin(v), pin(a), pin(ids)
@@ -257,7 +258,7 @@ def run_ours(args):
     for _ in range(args.e2e_steps):
         run.set_ions(hx, hv, hid, nid, a=ha)
         run.step(1)
-        hx, hv, ha, hid = run.get_ions()
+        run.get_ions(out=(hx, hv, ha, hid))
         nid = int(run.counters()[15])
         run.dust_state()
     torch.cuda.synchronize()

@@ -253,11 +253,13 @@ def od_dust_now(h, n_dust):
     return q[:n_dust], fo[: 3 * n_dust].reshape(n_dust, 3)
 
 
-def od_get_ions(h, cap):
-    x = np.zeros((cap, 3))
-    v = np.zeros((cap, 3))
-    a = np.zeros((cap, 3))
-    ids = np.zeros(cap, dtype=np.uint64)
+def od_get_ions(h, cap, out=None):
+    """(x, v, a, ids) of the current ions; out = (x, v, a, ids) host arrays of at least
+    cap rows (e.g. page-locked ones, which the library copies into directly) or None"""
+    if out is None:
+        out = (np.zeros((cap, 3)), np.zeros((cap, 3)), np.zeros((cap, 3)), np.zeros(cap, dtype=np.uint64))
+    x, v, a, ids = out
+    assert all(t.flags.c_contiguous and len(t) >= cap for t in out) and ids.dtype == np.uint64
     n = _check(lib().od_get_ions(h, _ptr(x), _ptr(v), _ptr(a), _ptr(ids), int(cap)), h)
     return x[:n], v[:n], a[:n], ids[:n]
 
@@ -531,8 +533,8 @@ class Run:
     def dust_now(self):
         return od_dust_now(self.h, self.D)
 
-    def get_ions(self):
-        return od_get_ions(self.h, max(int(od_info(self.h)["capacity"]), 1))
+    def get_ions(self, out=None):
+        return od_get_ions(self.h, max(int(od_info(self.h)["capacity"]), 1), out)
 
     def set_ions(self, x, v, ids, next_id, a=None):
         od_set_ions(self.h, x, v, ids, next_id, a)

@@ -262,6 +262,9 @@ struct od_handle {
     unsigned long long* d_hist = nullptr;  // n(r, z) counts [nz][nr] while enabled
     int hist_nr = 0, hist_nz = 0;
     long long hist_samples = 0;
+    double* d_io = nullptr;   // device staging of host arrays: x, v, a as [cap][3] each
+    double* h_io = nullptr;   // pinned staging for pageable host arrays (same layout)
+    uint64_t* h_ioid = nullptr;
     bool cut_on = false;                   // ion-ion cutoff (od_set_cutoff)
     double r_cut = 0.0, r_switch = 0.0;
     CutBufs C{};
@@ -666,6 +669,28 @@ int ensure_series(od_handle* h, long long need)
     return OD_OK;
 }
 
+// staging for host arrays crossing the ABI: one device buffer and one pinned host buffer
+// of 9 doubles per ion of capacity (x, v, a interleaved) plus the ids
+int ensure_io(od_handle* h)
+{
+    if (h->d_io) return OD_OK;
+    OD_CK(h, cudaMalloc(&h->d_io, sizeof(double) * 9 * h->cap));
+    OD_CK(h, cudaMallocHost(&h->h_io, sizeof(double) * 9 * h->cap));
+    OD_CK(h, cudaMallocHost(&h->h_ioid, sizeof(uint64_t) * h->cap));
+    return OD_OK;
+}
+
+// host memory the GPU can copy from directly (page-locked or registered)
+bool host_pinned(const void* p)
+{
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeHost;
+}
+
 void free_cut(od_handle* h)
 {
     CutBufs& C = h->C;
@@ -695,6 +720,9 @@ void free_all(od_handle* h)
     cudaFree(h->d_series);
     cudaFree(h->d_evseries);
     cudaFree(h->d_hist);
+    cudaFree(h->d_io);
+    cudaFreeHost(h->h_io);
+    cudaFreeHost(h->h_ioid);
     free_cut(h);
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
     if (h->graph) cudaGraphDestroy(h->graph);
@@ -947,36 +975,30 @@ int64_t od_get_ions(od_handle* h, double* x, double* v, double* a, uint64_t* id,
     if (!h) return fail(h, OD_EINVAL, "bad handle");
     const long long N = h->P.N;
     if ((x || v || a || id) && cap < N) return fail(h, OD_EINVAL, "host arrays too small");
+    if (N == 0 || !(x || v || a || id)) return N;
+    int rc;
+    if ((rc = ensure_io(h))) return rc;
     const int buf = (int)(h->host_step & 1);
-    std::vector<double> tmp(3 * (size_t)N);
-    auto inter = [&](const double* d, double* o) -> int {
-        for (int c = 0; c < 3; ++c)
-            OD_CK(h, cudaMemcpyAsync(tmp.data() + c * N, d + c * h->cap, sizeof(double) * N, cudaMemcpyDeviceToHost,
-                                     h->stream));
-        OD_CK(h, cudaStreamSynchronize(h->stream));
-        for (long long i = 0; i < N; ++i)
-            for (int c = 0; c < 3; ++c) o[3 * i + c] = tmp[c * N + i];
-        return OD_OK;
-    };
-    if (N > 0) {
-        int rc;
-        if (x && (rc = inter(h->B.x[buf], x))) return rc;
-        if (v && (rc = inter(h->B.v[buf], v))) return rc;
-        if (a) {
-            std::vector<float4> ta(N);
-            OD_CK(h, cudaMemcpyAsync(ta.data(), h->B.acc, sizeof(float4) * N, cudaMemcpyDeviceToHost, h->stream));
-            OD_CK(h, cudaStreamSynchronize(h->stream));
-            for (long long i = 0; i < N; ++i) {
-                a[3 * i] = ta[i].x;
-                a[3 * i + 1] = ta[i].y;
-                a[3 * i + 2] = ta[i].z;
-            }
-        }
-        if (id) {
-            OD_CK(h, cudaMemcpyAsync(id, h->B.id[buf], sizeof(uint64_t) * N, cudaMemcpyDeviceToHost, h->stream));
-            OD_CK(h, cudaStreamSynchronize(h->stream));
-        }
+    const size_t bytes = sizeof(double) * 3 * N;
+    double* const outs[3] = {x, v, a};
+    bool staged[3] = {false, false, false};
+    for (int k = 0; k < 3; ++k) {
+        if (!outs[k]) continue;
+        double* dst = h->d_io + 3 * h->cap * k;
+        if (k < 2) OD_LK(h, launch_layout(1, k == 0 ? h->B.x[buf] : h->B.v[buf], dst, (int)N, h->cap, h->stream));
+        else OD_LK(h, launch_layout(2, h->B.acc, dst, (int)N, h->cap, h->stream));
+        staged[k] = !host_pinned(outs[k]);
+        OD_CK(h, cudaMemcpyAsync(staged[k] ? h->h_io + 3 * h->cap * k : outs[k], dst, bytes, cudaMemcpyDeviceToHost,
+                                 h->stream));
     }
+    const bool id_staged = id && !host_pinned(id);
+    if (id)
+        OD_CK(h, cudaMemcpyAsync(id_staged ? h->h_ioid : id, h->B.id[buf], sizeof(uint64_t) * N,
+                                 cudaMemcpyDeviceToHost, h->stream));
+    OD_CK(h, cudaStreamSynchronize(h->stream));
+    for (int k = 0; k < 3; ++k)
+        if (staged[k]) std::memcpy(outs[k], h->h_io + 3 * h->cap * k, bytes);
+    if (id_staged) std::memcpy(id, h->h_ioid, sizeof(uint64_t) * N);
     return N;
 }
 
@@ -987,21 +1009,29 @@ int od_set_ions(od_handle* h, const double* x, const double* v, const double* a,
     if (h->batch_member) return fail(h, OD_EINVAL, "the ions of a batch member cannot be replaced");
     if (n > h->cap) return fail(h, OD_EOVERFLOW, "more ions than the handle's capacity");
     const int buf = (int)(h->host_step & 1);
-    std::vector<double> tmp(3 * (size_t)n);
-    auto upload = [&](const double* src, double* d) -> int {
-        for (int64_t i = 0; i < n; ++i)
-            for (int c = 0; c < 3; ++c) tmp[c * n + i] = src[3 * i + c];
-        for (int c = 0; c < 3; ++c)
-            OD_CK(h, cudaMemcpyAsync(d + c * h->cap, tmp.data() + c * n, sizeof(double) * n, cudaMemcpyHostToDevice,
-                                     h->stream));
-        OD_CK(h, cudaStreamSynchronize(h->stream));
-        return OD_OK;
-    };
     int rc;
     if (n > 0) {
-        if ((rc = upload(x, h->B.x[buf]))) return rc;
-        if ((rc = upload(v, h->B.v[buf]))) return rc;
-        OD_CK(h, cudaMemcpyAsync(h->B.id[buf], id, sizeof(uint64_t) * n, cudaMemcpyHostToDevice, h->stream));
+        if ((rc = ensure_io(h))) return rc;
+        const size_t bytes = sizeof(double) * 3 * n;
+        const double* const ins[3] = {x, v, a};
+        for (int k = 0; k < 3; ++k) {
+            if (!ins[k]) continue;
+            double* dst = h->d_io + 3 * h->cap * k;
+            const double* src = ins[k];
+            if (!host_pinned(src)) {
+                std::memcpy(h->h_io + 3 * h->cap * k, src, bytes);
+                src = h->h_io + 3 * h->cap * k;
+            }
+            OD_CK(h, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, h->stream));
+            if (k < 2) OD_LK(h, launch_layout(0, dst, k == 0 ? h->B.x[buf] : h->B.v[buf], (int)n, h->cap, h->stream));
+            else OD_LK(h, launch_layout(3, dst, h->B.acc, (int)n, h->cap, h->stream));
+        }
+        const uint64_t* ids = id;
+        if (!host_pinned(id)) {
+            std::memcpy(h->h_ioid, id, sizeof(uint64_t) * n);
+            ids = h->h_ioid;
+        }
+        OD_CK(h, cudaMemcpyAsync(h->B.id[buf], ids, sizeof(uint64_t) * n, cudaMemcpyHostToDevice, h->stream));
     }
     unsigned long long nid = next_id;
     OD_CK(h, cudaMemcpyAsync((char*)h->B.ctrl + offsetof(Ctrl, next_id), &nid, sizeof(nid), cudaMemcpyHostToDevice,
@@ -1009,15 +1039,8 @@ int od_set_ions(od_handle* h, const double* x, const double* v, const double* a,
     if ((rc = replan(h, (int)n))) return rc;
     h->graph_ok = false;
     OD_LK(h, launch_fpos(h->P, h->B, buf, h->stream));
-    if (a) {
-        std::vector<float4> ta(std::max<int64_t>(n, 1));
-        for (int64_t i = 0; i < n; ++i) ta[i] = make_float4((float)a[3 * i], (float)a[3 * i + 1], (float)a[3 * i + 2], 0.f);
-        if (n > 0)
-            OD_CK(h, cudaMemcpyAsync(h->B.acc, ta.data(), sizeof(float4) * n, cudaMemcpyHostToDevice, h->stream));
-        OD_CK(h, cudaStreamSynchronize(h->stream));
-    } else {
-        if ((rc = force_eval(h))) return rc;
-    }
+    // given accelerations were converted on the device above; otherwise evaluate them
+    if (!a && (rc = force_eval(h))) return rc;
     return read_error_word(h);
 }
 

@@ -162,6 +162,9 @@ int launch_forces(const Phys& P, const Bufs& B, const ForceArgs& F, int variant,
 int launch_kick(const Phys& P, const Bufs& B, const ForceArgs& F, int mode, cudaStream_t s);
 int launch_dust(const Phys& P, const Bufs& B, int mode, cudaStream_t s);
 int launch_stats(const Phys& P, const Bufs& B, double* mean_se, cudaStream_t s);
+// kind 0: [n][3] -> [3][cap] doubles; 1: [3][cap] -> [n][3]; 2: float4 -> [n][3] doubles;
+// 3: [n][3] doubles -> float4
+int launch_layout(int kind, const void* src, void* dst, int n, long long cap, cudaStream_t s);
 int launch_hist(const Phys& P, const Bufs& B, unsigned long long* counts, int nr, int nz, double inv_dr,
                 double inv_dz, int sms, cudaStream_t s);
 int launch_eout_grid(double R, double H, double lam, int nx, int nz, int nq, const double* gl_x,

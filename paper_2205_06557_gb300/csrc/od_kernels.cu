@@ -300,6 +300,58 @@ int launch_dust(const Phys& P, const Bufs& B, int mode, cudaStream_t s)
     return ck(cudaGetLastError());
 }
 
+// host interface layouts: the ABI's interleaved [n][3] arrays <-> the device's [3][cap]
+// structure of arrays (and the float4 accelerations), converted on the device so that a
+// host array moves as one contiguous copy
+__global__ void k_aos_to_soa(const double* __restrict__ aos, double* __restrict__ soa, int n, long long cap)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    soa[i] = aos[3 * (long long)i];
+    soa[cap + i] = aos[3 * (long long)i + 1];
+    soa[2 * cap + i] = aos[3 * (long long)i + 2];
+}
+
+__global__ void k_soa_to_aos(const double* __restrict__ soa, double* __restrict__ aos, int n, long long cap)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    aos[3 * (long long)i] = soa[i];
+    aos[3 * (long long)i + 1] = soa[cap + i];
+    aos[3 * (long long)i + 2] = soa[2 * cap + i];
+}
+
+__global__ void k_acc_to_aos(const float4* __restrict__ acc, double* __restrict__ aos, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float4 a = acc[i];
+    aos[3 * (long long)i] = a.x;
+    aos[3 * (long long)i + 1] = a.y;
+    aos[3 * (long long)i + 2] = a.z;
+}
+
+__global__ void k_aos_to_acc(const double* __restrict__ aos, float4* __restrict__ acc, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    acc[i] = make_float4((float)aos[3 * (long long)i], (float)aos[3 * (long long)i + 1], (float)aos[3 * (long long)i + 2],
+                         0.f);
+}
+
+int launch_layout(int kind, const void* src, void* dst, int n, long long cap, cudaStream_t s)
+{
+    if (n <= 0) return 0;
+    const int g = (n + 255) / 256;
+    switch (kind) {
+    case 0: k_aos_to_soa<<<g, 256, 0, s>>>((const double*)src, (double*)dst, n, cap); break;
+    case 1: k_soa_to_aos<<<g, 256, 0, s>>>((const double*)src, (double*)dst, n, cap); break;
+    case 2: k_acc_to_aos<<<g, 256, 0, s>>>((const float4*)src, (double*)dst, n); break;
+    default: k_aos_to_acc<<<g, 256, 0, s>>>((const double*)src, (float4*)dst, n); break;
+    }
+    return ck(cudaGetLastError());
+}
+
 // n(r, z) binning of the ions at the end of a step (observability): bin indices from
 // the FP64 positions with explicitly rounded operations (no contraction), so a host
 // binning that evaluates r = sqrt(x*x + y*y), r * (nr / R) and (z + H/2) * (nz / H)
