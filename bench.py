@@ -185,7 +185,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": desc, "n_ions": n},
+            "data": "synthetic", "config": {"workload": desc, "n_ions": n, "n_dust": len(p["dust"])},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
                              "sample": "each step: FP64 oracle pair forces of %d target ions against all %d ions"
                                        % (m, n)},
