@@ -24,6 +24,7 @@ F_NO_EOUT = 2
 F_NO_BOUNDARY = 4
 F_NO_ABSORB = 8
 F_PAPER_SIDE = 16
+F_FLUX_INJECT = 32
 
 Q_MODELS = {"given": 0, "consistent": 1}
 
@@ -81,6 +82,8 @@ def lib():
         L.orc_cyl_integral.restype = d
         L.orc_cyl_integral.argtypes = [P(_Params), d, d]
         L.orc_inject_sample.argtypes = [vp, u64, ctypes.c_uint32, vp, vp, vp]
+        L.orc_injections.restype = i64
+        L.orc_injections.argtypes = [vp, ctypes.c_uint32]
         L.orc_records.argtypes = [vp, i64, i64, vp, vp]
         L.orc_dust_q.argtypes = [vp, vp]
         L.orc_dust_terms.argtypes = [vp, vp, vp]
@@ -218,6 +221,10 @@ class Oracle:
         fo = np.zeros((MAX_DUST, 3))
         lib().orc_forces(self.h, int(i0), int(i1), _ptr(acc), _ptr(fo) if dust else None)
         return acc, fo[: self.D]
+
+    def injections(self, step):
+        """superions injected in step `step` (1-based) under the flux rule"""
+        return lib().orc_injections(self.h, int(step))
 
     def derived(self):
         o = np.zeros(24)

@@ -45,7 +45,7 @@ static const double ME = 9.1093837015e-31;   /* kg */
 #define TWO32 4294967296.0
 
 /* Philox streams (fourth counter word) */
-enum { ST_INIT_POS = 0, ST_INIT_VEL = 1, ST_COLL = 2, ST_COLL_VEL = 3, ST_INJ_A = 4, ST_INJ_B = 5 };
+enum { ST_INIT_POS = 0, ST_INIT_VEL = 1, ST_COLL = 2, ST_COLL_VEL = 3, ST_INJ_A = 4, ST_INJ_B = 5, ST_INJ_N = 6 };
 
 struct orc_state {
     orc_params p;
@@ -61,6 +61,7 @@ struct orc_state {
     double pcoll;
     double alpha[15];
     double Ie0;   /* electron flux per unit area at zero potential, 1/(m^2 s) */
+    double inj_rate; /* superions entering through the three faces per second (App. B) */
     int64_t N, next_id, step;
     double *x, *v, *a;
     uint64_t* id;
@@ -553,6 +554,7 @@ orc_state* orc_create(const orc_params* pin, char* err, int errlen)
     double Jt = PI * p->R * p->R * (-s->u * ncdf(-zu) + s->sig * npdf(zu));
     double Js = 2.0 * PI * p->R * p->H * s->sig / sqrt(2.0 * PI);
     double J = Jb + Jt + Js;
+    s->inj_rate = p->n_inf / p->weight * J;
     s->pb = Jb / J;
     s->pt = Jt / J;
     s->ps = Js / J;
@@ -717,6 +719,35 @@ static void grow_records(orc_state* s, int64_t need)
 }
 
 /* one time step s -> s+1 in the canonical order */
+/* Number of superions injected in a step when the count follows the fluxes: Poisson
+ * with mean lam = inj_rate dt.  lam is split into chunks of at most 64; each chunk is
+ * drawn by inversion, summing e^-l l^x / x! in increasing x until the sum reaches one
+ * uniform U = (w + 1/2) 2^-32.  Uniform j of step s is word j mod 4 of the Philox block
+ * with counter (j / 4, 0, s, stream 6). */
+static int64_t poisson_injections(const orc_state* s, uint32_t sn)
+{
+    double rem = s->inj_rate * s->p.dt;
+    int64_t k = 0;
+    for (int j = 0; rem > 0.0; ++j) {
+        const double l = rem > 64.0 ? 64.0 : rem;
+        rem -= l;
+        uint32_t w[4];
+        draw(s, (uint64_t)(j >> 2), sn, ST_INJ_N, w);
+        const double U = unif(w[j & 3]);
+        double pr = exp(-l), F = pr;
+        int64_t x = 0;
+        while (U > F && x < 100000) {
+            ++x;
+            pr = pr * (l / (double)x);
+            F += pr;
+        }
+        k += x;
+    }
+    return k;
+}
+
+int64_t orc_injections(const orc_state* s, uint32_t step) { return poisson_injections(s, step); }
+
 static void step_once(orc_state* s)
 {
     const orc_params* p = &s->p;
@@ -778,24 +809,34 @@ static void step_once(orc_state* s)
         ++w;
     }
     int64_t removed = N - w;
+    /* 1:1 replacement keeps N; with the flux rule a Poisson count enters instead */
+    const int64_t nin = (p->flags & ORC_F_FLUX_INJECT) ? poisson_injections(s, sn) : removed;
+    if (w + nin > N) {
+        const int64_t cnt = w + nin;
+        s->x = realloc(s->x, sizeof(double) * 3 * cnt);
+        s->v = realloc(s->v, sizeof(double) * 3 * cnt);
+        s->a = realloc(s->a, sizeof(double) * 3 * cnt);
+        s->id = realloc(s->id, sizeof(uint64_t) * cnt);
+    }
     int64_t inj[3] = {0, 0, 0};
-    for (int64_t r = 0; r < removed; ++r) {
+    for (int64_t r = 0; r < nin; ++r) {
         uint64_t nid = (uint64_t)(s->next_id + r);
         int face;
         orc_inject_sample(s, nid, sn, &s->x[3 * (w + r)], &s->v[3 * (w + r)], &face);
         s->id[w + r] = nid;
         inj[face] += 1;
     }
-    s->next_id += removed;
+    s->next_id += nin;
+    s->N = w + nin;
     free(cls);
 
     /* 4. forces at the new positions, with the charges of the previous step */
     double fo[ORC_MAX_DUST * 3];
-    orc_forces(s, 0, N, s->a, fo);
+    orc_forces(s, 0, s->N, s->a, fo);
 
     /* 5. second half kick; 6. Andersen collisions with neutrals (Sec. 2) */
     int64_t ncoll = 0;
-    for (int64_t i = 0; i < N; ++i) {
+    for (int64_t i = 0; i < s->N; ++i) {
         for (int c = 0; c < 3; ++c) s->v[3 * i + c] += 0.5 * dt * s->a[3 * i + c];
         uint32_t wd[4];
         draw(s, s->id[i], sn, ST_COLL, wd);

@@ -29,6 +29,8 @@
 #define ORC_F_NO_BOUNDARY 4   /* no outflow removal, no injection */
 #define ORC_F_NO_ABSORB   8   /* dust does not absorb ions */
 #define ORC_F_PAPER_SIDE 16   /* side injection without tangential velocity */
+#define ORC_F_FLUX_INJECT 32  /* inject a Poisson number of ions per step from the App. B
+                                 fluxes instead of replacing each removed ion (N varies) */
 
 #define ORC_Q_GIVEN 0
 #define ORC_Q_CONSISTENT 1
@@ -86,6 +88,8 @@ void orc_records(const orc_state* s, int64_t first, int64_t count, double* rec, 
 void orc_dust_q(const orc_state* s, double* q);
 int orc_dust_terms(const orc_state* s, double* mean, double* se);
 void orc_philox(const uint32_t key[2], const uint32_t ctr[4], uint32_t out[4]);
+/* injected superions of step `step` (1-based) under the flux rule (ORC_F_FLUX_INJECT) */
+int64_t orc_injections(const orc_state* s, uint32_t step);
 int orc_num_threads(void);
 
 #endif
