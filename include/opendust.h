@@ -54,6 +54,11 @@ extern "C" {
 #define OD_F_FP32_STATE 32  /* round ion positions and velocities to FP32 after every
                                update (precision study: FP32-only ion state) */
 #define OD_F_NO_GRAPH 64    /* launch each step's kernels directly, not as a CUDA graph */
+#define OD_F_FLUX_INJECT 128 /* inject a Poisson number of ions per step with the mean
+                                n_inf (J_bottom + J_top + J_side) dt / weight of the App. B
+                                fluxes, instead of one per removed ion: N varies (within a
+                                capacity of 1.25 N0 + 256; beyond it a step reports
+                                OD_EOVERFLOW); single runs without the cutoff only */
 
 /* od_params.charge_model (Sec. 2 charging options) */
 #define OD_Q_GIVEN 0      /* constant charges q0 */
@@ -197,7 +202,9 @@ int od_density_enable(od_handle* h, int32_t nr, int32_t nz);
 int od_density_read(od_handle* h, uint64_t* counts, double* density, int64_t* samples);
 
 /* Derived constants (host double[32]): lambda_De, c_s, sig_i, sig_n, u, E, q, m, p_bottom,
- * p_top, p_side, T_bottom, T_bottom+top, T_coll, N, alpha[0..14] (at 15..29), capacity, SMs. */
+ * p_top, p_side, T_bottom, T_bottom+top, T_coll, N (the ion count the buffers and kernel
+ * plans are sized for: under OD_F_FLUX_INJECT the capacity, and the live count is
+ * od_counters()[14]), alpha[0..14] (at 15..29), capacity, SMs. */
 int od_info(od_handle* h, double* out);
 
 /* Per-kernel timing (profiling mode): when on, od_step launches kernels directly with

@@ -33,6 +33,7 @@ F_NO_ABSORB = 8
 F_PAPER_SIDE = 16
 F_FP32_STATE = 32
 F_NO_GRAPH = 64
+F_FLUX_INJECT = 128
 
 Q_GIVEN = 0
 Q_CONSISTENT = 1

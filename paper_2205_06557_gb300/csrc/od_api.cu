@@ -388,6 +388,7 @@ void derive(const od_params* p, Phys& P, od_handle* h)
     const double Jt = kPI * p->R * p->R * (-P.u * norm_cdf(-zu) + P.sig * norm_pdf(zu));
     const double Js = 2.0 * kPI * p->R * p->H * P.sig / std::sqrt(2.0 * kPI);
     const double J = Jb + Jt + Js;
+    P.inj_lambda = p->n_inf / p->weight * J * p->dt;
     P.Tb = prob_threshold(Jb / J);
     P.Tbt = prob_threshold((Jb + Jt) / J);
     const double pc = -std::expm1(-p->nu_in * p->dt);
@@ -593,6 +594,12 @@ int launch_pairs(od_handle* h)
     return launch_forces(h->P, h->B, h->F, h->variant, h->stream);
 }
 
+// ion count the plans are made for: the live count, or the capacity under the flux rule
+int plan_n(const od_handle* h, long long n_live)
+{
+    return (h->P.flags & OD_F_FLUX_INJECT) ? (int)h->cap : (int)n_live;
+}
+
 int read_error_word(od_handle* h)
 {
     int err = 0;
@@ -764,8 +771,11 @@ int create_impl(const od_params* p, od_handle* h)
         if (rc) return rc;
     }
     set_field_coeffs(h->P, h->alpha, eout_on);
-    const int N = h->P.N;
-    h->cap = std::max(N, 1);
+    const int N = h->P.N;  // initial ions
+    // with the flux injection rule N varies: buffers and plans are sized for a capacity
+    const bool flux = (p->flags & OD_F_FLUX_INJECT) != 0;
+    const int n_plan = flux ? N + std::max(256, (N + 3) / 4) : N;
+    h->cap = std::max(n_plan, 1);
     h->npad_cap = ((long long)h->cap + 1023) / 1024 * 1024;
     h->nb_cap = (h->cap + kick_block() - 1) / kick_block();
     // untuned runs start from the size-based default; batch members are re-planned by
@@ -791,12 +801,15 @@ int create_impl(const od_params* p, od_handle* h)
     Ctrl c0;
     std::memset(&c0, 0, sizeof(c0));
     c0.next_id = (unsigned long long)N;
+    c0.n_cur = N;
     for (int k = 0; k < p->n_dust; ++k)
         c0.Q[k] = p->charge_model == OD_Q_OML ? oml_charge(p, p->dust[k].radius) : p->dust[k].q0;
     OD_CK(h, cudaMemcpyAsync(B.ctrl, &c0, sizeof(Ctrl), cudaMemcpyHostToDevice, h->stream));
-    int rc = replan(h, N);
+    int rc = replan(h, n_plan);
     if (rc) return rc;
-    OD_LK(h, launch_init_ions(h->P, B, h->stream));
+    Phys Pi = h->P;
+    Pi.N = N;  // the initial ions only
+    OD_LK(h, launch_init_ions(Pi, B, h->stream));
     OD_LK(h, launch_fpos(h->P, B, 0, h->stream));
     rc = force_eval(h);
     if (rc) return rc;
@@ -948,11 +961,14 @@ int od_series(od_handle* h, int64_t first, int64_t count, double* rec, int32_t* 
 int od_counters(od_handle* h, int64_t* out)
 {
     if (!h || !out) return fail(h, OD_EINVAL, "bad argument");
+    int n_live = 0;
     OD_CK(h, cudaMemcpyAsync(out, (char*)h->B.ctrl + offsetof(Ctrl, counters), sizeof(long long) * OD_NCOUNT,
                              cudaMemcpyDeviceToHost, h->stream));
+    OD_CK(h, cudaMemcpyAsync(&n_live, (char*)h->B.ctrl + offsetof(Ctrl, n_cur), sizeof(int), cudaMemcpyDeviceToHost,
+                             h->stream));
     OD_CK(h, cudaStreamSynchronize(h->stream));
     out[13] = h->host_step;
-    out[14] = h->P.N;
+    out[14] = n_live;  // ions alive now (varies under the flux rule)
     return OD_OK;
 }
 
@@ -973,7 +989,11 @@ int od_dust_now(od_handle* h, double* q, double* f_orbit)
 int64_t od_get_ions(od_handle* h, double* x, double* v, double* a, uint64_t* id, int64_t cap)
 {
     if (!h) return fail(h, OD_EINVAL, "bad handle");
-    const long long N = h->P.N;
+    int n_live = 0;  // ions alive (it varies under the flux rule)
+    OD_CK(h, cudaMemcpyAsync(&n_live, (char*)h->B.ctrl + offsetof(Ctrl, n_cur), sizeof(int), cudaMemcpyDeviceToHost,
+                             h->stream));
+    OD_CK(h, cudaStreamSynchronize(h->stream));
+    const long long N = n_live;
     if ((x || v || a || id) && cap < N) return fail(h, OD_EINVAL, "host arrays too small");
     if (N == 0 || !(x || v || a || id)) return N;
     int rc;
@@ -1036,7 +1056,11 @@ int od_set_ions(od_handle* h, const double* x, const double* v, const double* a,
     unsigned long long nid = next_id;
     OD_CK(h, cudaMemcpyAsync((char*)h->B.ctrl + offsetof(Ctrl, next_id), &nid, sizeof(nid), cudaMemcpyHostToDevice,
                              h->stream));
-    if ((rc = replan(h, (int)n))) return rc;
+    const int n_live = (int)n;
+    OD_CK(h, cudaMemcpyAsync((char*)h->B.ctrl + offsetof(Ctrl, n_cur), &n_live, sizeof(int), cudaMemcpyHostToDevice,
+                             h->stream));
+    OD_CK(h, cudaStreamSynchronize(h->stream));  // n_live is a host local
+    if ((rc = replan(h, plan_n(h, n)))) return rc;
     h->graph_ok = false;
     OD_LK(h, launch_fpos(h->P, h->B, buf, h->stream));
     // given accelerations were converted on the device above; otherwise evaluate them
@@ -1048,6 +1072,7 @@ int od_set_cutoff(od_handle* h, double r_cut, double r_switch)
 {
     if (!h) return fail(h, OD_EINVAL, "bad handle");
     if (h->batch_member) return fail(h, OD_EINVAL, "the cutoff is set on single runs, not batch members");
+    if (h->P.flags & OD_F_FLUX_INJECT) return fail(h, OD_EINVAL, "the cutoff needs a fixed ion count (no flux rule)");
     if (!std::isfinite(r_cut) || !std::isfinite(r_switch)) return fail(h, OD_EINVAL, "cutoff: non-finite distance");
     OD_CK(h, cudaStreamSynchronize(h->stream));
     int rc;
@@ -1541,7 +1566,7 @@ int od_load(const char* path, void* cuda_stream, od_handle** out)
     if (hd.variant >= 0 && hd.variant < num_force_variants()) {
         if ((rc = apply_force_config(h, hd.variant, hd.upb, hd.bps))) return done(rc);
     } else {
-        if ((rc = replan(h, (int)N))) return done(rc);
+        if ((rc = replan(h, plan_n(h, N)))) return done(rc);
         if (launch_fpos(h->P, h->B, buf, h->stream)) return done(fail(h, OD_ECUDA, "position refresh failed"));
     }
     h->graph_ok = false;
@@ -1694,6 +1719,8 @@ int od_create_batch(const od_params* ps, int32_t R, od_batch** out)
         std::string msg;
         const int rc = validate(ps + r, msg);
         if (rc) return bfail(nullptr, rc, "run " + std::to_string(r) + ": " + msg);
+        if (ps[r].flags & OD_F_FLUX_INJECT)
+            return bfail(nullptr, OD_EINVAL, "run " + std::to_string(r) + ": batched runs keep a fixed ion count");
     }
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return bfail(nullptr, OD_ENODEV, "no CUDA device");

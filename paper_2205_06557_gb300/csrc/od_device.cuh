@@ -182,6 +182,32 @@ __device__ __forceinline__ float4 scaled(const Phys& P, double x, double y, doub
 
 __device__ __forceinline__ double rnd32(double v) { return (double)(float)v; }
 
+// Number of superions injected in step sn under the flux rule: Poisson with mean lam,
+// split into chunks of at most 64, each drawn by inversion (summing e^-l l^x / x! in
+// increasing x until the sum reaches one uniform); uniform j of the step is word j mod 4
+// of the Philox block with counter (j / 4, 0, sn, ST_INJ_N).  FP64 throughout.
+__device__ __forceinline__ int poisson_injections(const Phys& P, uint32_t sn)
+{
+    double rem = P.inj_lambda;
+    int k = 0;
+    for (int j = 0; rem > 0.0; ++j) {
+        const double l = rem > 64.0 ? 64.0 : rem;
+        rem -= l;
+        const uint4 w = philox(P, (unsigned long long)(j >> 2), sn, ST_INJ_N);
+        const uint32_t wj = (j & 3) == 0 ? w.x : (j & 3) == 1 ? w.y : (j & 3) == 2 ? w.z : w.w;
+        const double U = unif(wj);
+        double pr = exp(-l), F = pr;
+        int x = 0;
+        while (U > F && x < 100000) {
+            ++x;
+            pr = pr * (l / (double)x);
+            F += pr;
+        }
+        k += x;
+    }
+    return k;
+}
+
 // ------------------------------------------------- push + scan + compaction
 constexpr int PUSH_BT = 256;
 
@@ -199,13 +225,17 @@ __device__ __forceinline__ void push_scan_body(const Phys& P, const Bufs& B, int
 {
     __shared__ unsigned s_tile;
     __shared__ int s_wsum[BT / 32];
-    __shared__ int s_total, s_prefix, s_last, s_m;
+    __shared__ int s_total, s_prefix, s_last, s_m, s_k;
     __shared__ int s_face[3];
     Ctrl* C = B.ctrl;
     const long long step = C->step;
     const int src = (int)(step & 1), dst = src ^ 1;
     const uint32_t sn = (uint32_t)(step + 1);
     const long long cap = B.cap;
+    const bool flux = (P.flags & OD_F_FLUX_INJECT) != 0;
+    // ions alive at the start of the step (only the last tile, after every other tile
+    // has finished, writes the new count)
+    const int n_live = *(volatile int*)&C->n_cur;
     if (threadIdx.x == 0) s_tile = given_tile >= 0 ? (unsigned)given_tile : atomicAdd(&C->tile_counter, 1u);
     __syncthreads();
     const int tile = (int)s_tile;
@@ -215,7 +245,7 @@ __device__ __forceinline__ void push_scan_body(const Phys& P, const Bufs& B, int
     double x = 0, y = 0, z = 0, vx = 0, vy = 0, vz = 0;
     unsigned long long id = 0;
     int cls = -2;  // -2 stays, -1 outflow, k >= 0 absorbed by grain k
-    if (i < P.N) {
+    if (i < n_live) {
         const double* X = B.x[src];
         const double* V = B.v[src];
         x = X[i];
@@ -337,7 +367,7 @@ __device__ __forceinline__ void push_scan_body(const Phys& P, const Bufs& B, int
     __syncthreads();
     const int prefix = s_prefix;
 
-    if (i < P.N) {
+    if (i < n_live) {
         if (!removed) {
             const int d = i - prefix - lrank;  // stable compaction
             double* X = B.x[dst];
@@ -359,14 +389,16 @@ __device__ __forceinline__ void push_scan_body(const Phys& P, const Bufs& B, int
             rm.cls = cls;
             rm.pad = 0;
             B.rem[r] = rm;
-            Inj in;
-            sample_injection(P, C->next_id + (unsigned long long)r, sn, in);
-            if (P.flags & OD_F_FP32_STATE) {
-                in.x = rnd32(in.x), in.y = rnd32(in.y), in.z = rnd32(in.z);
-                in.vx = rnd32(in.vx), in.vy = rnd32(in.vy), in.vz = rnd32(in.vz);
+            if (!flux) {  // 1:1 replacement: the removed ion's thread samples its successor
+                Inj in;
+                sample_injection(P, C->next_id + (unsigned long long)r, sn, in);
+                if (P.flags & OD_F_FP32_STATE) {
+                    in.x = rnd32(in.x), in.y = rnd32(in.y), in.z = rnd32(in.z);
+                    in.vx = rnd32(in.vx), in.vy = rnd32(in.vy), in.vz = rnd32(in.vz);
+                }
+                in.pad = 0;
+                B.inj[r] = in;
             }
-            in.pad = 0;
-            B.inj[r] = in;
         }
     }
 
@@ -380,18 +412,39 @@ __device__ __forceinline__ void push_scan_body(const Phys& P, const Bufs& B, int
     if (threadIdx.x < 3) s_face[threadIdx.x] = 0;
     if (threadIdx.x == 0) {
         int m = *(volatile int*)&C->removed_total;
-        if (m > P.N) m = P.N;
+        if (m > n_live) m = n_live;
         s_m = m;
+        // injections: one per removed ion, or a Poisson number from the fluxes (clamped
+        // to the capacity, which reports an overflow)
+        int k = flux ? poisson_injections(P, sn) : m;
+        if (n_live - m + k > P.N) {
+            k = P.N - (n_live - m);
+            atomicOr(&C->err, ERR_OVERFLOW);
+        }
+        s_k = k;
     }
     __syncthreads();
-    const int m = s_m;
-    for (int r = threadIdx.x; r < m; r += BT) {
-        const Inj* in = B.inj + r;
-        const double ix = __ldcg(&in->x), iy = __ldcg(&in->y), iz = __ldcg(&in->z);
-        const double ivx = __ldcg(&in->vx), ivy = __ldcg(&in->vy), ivz = __ldcg(&in->vz);
-        const unsigned long long iid = __ldcg(&in->id);
-        const int face = __ldcg(&in->face);
-        const int d = P.N - m + r;
+    const int m = s_m, kin = s_k;
+    for (int r = threadIdx.x; r < kin; r += BT) {
+        double ix, iy, iz, ivx, ivy, ivz;
+        unsigned long long iid;
+        int face;
+        if (flux) {
+            Inj in;
+            sample_injection(P, C->next_id + (unsigned long long)r, sn, in);
+            if (P.flags & OD_F_FP32_STATE) {
+                in.x = rnd32(in.x), in.y = rnd32(in.y), in.z = rnd32(in.z);
+                in.vx = rnd32(in.vx), in.vy = rnd32(in.vy), in.vz = rnd32(in.vz);
+            }
+            ix = in.x, iy = in.y, iz = in.z, ivx = in.vx, ivy = in.vy, ivz = in.vz, iid = in.id, face = in.face;
+        } else {
+            const Inj* in = B.inj + r;
+            ix = __ldcg(&in->x), iy = __ldcg(&in->y), iz = __ldcg(&in->z);
+            ivx = __ldcg(&in->vx), ivy = __ldcg(&in->vy), ivz = __ldcg(&in->vz);
+            iid = __ldcg(&in->id);
+            face = __ldcg(&in->face);
+        }
+        const int d = n_live - m + r;
         double* X = B.x[dst];
         double* V = B.v[dst];
         X[d] = ix;
@@ -404,12 +457,19 @@ __device__ __forceinline__ void push_scan_body(const Phys& P, const Bufs& B, int
         B.fpos[d] = scaled(P, ix, iy, iz, ls_inv);
         atomicAdd(&s_face[face], 1);
     }
+    // slots vacated when fewer ions entered than left: far-away dummies for the pair kernel
+    const int n_new = n_live - m + kin;
+    for (int d = n_new + threadIdx.x; d < n_live; d += BT) {
+        const float far = 3.0e4f + 7.0f * (float)(d - n_new);
+        B.fpos[d] = make_float4(far, far, far, 0.0f);
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         C->ev_step[9] += s_face[0];
         C->ev_step[10] += s_face[1];
         C->ev_step[11] += s_face[2];
-        C->next_id += (unsigned long long)m;
+        C->next_id += (unsigned long long)kin;
+        C->n_cur = n_new;
         C->tile_counter = 0u;
         C->done_counter = 0u;
     }
@@ -915,7 +975,7 @@ __device__ __forceinline__ void kick_body(const Phys& P, const Bufs& B, const Fo
     const int buf = mode == 0 ? (int)((step + 1) & 1) : (int)(step & 1);
     const uint32_t sn = (uint32_t)(step + 1);
     const int i = blk * BT + threadIdx.x;
-    const bool live = i < P.N;
+    const bool live = i < C->n_cur;
     const long long cap = B.cap;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     double x = 0, y = 0, z = 0;
@@ -1148,7 +1208,7 @@ __device__ __forceinline__ void dust_body(const Phys& P, const Bufs& B, int nb, 
         C->ev_step[j] = 0;
     } else if (j == 32) {
         C->counters[13] = sn;
-        C->counters[14] = P.N;
+        C->counters[14] = C->n_cur;
         C->counters[15] = (long long)C->next_id;
         if (sn >= P.avg_start) C->wcount += 1;
         C->removed_total = 0;

@@ -24,7 +24,15 @@ constexpr long long SPIN_LIMIT = 1ll << 22;  // ~4 s of polling with the 1 us ba
 constexpr int VTAB_K = 4096;                  // intervals of the tabulated inverse flux CDFs
 
 // Philox streams (fourth counter word): the same layout on host and device.
-enum : uint32_t { ST_INIT_POS = 0, ST_INIT_VEL = 1, ST_COLL = 2, ST_COLL_VEL = 3, ST_INJ_A = 4, ST_INJ_B = 5 };
+enum : uint32_t {
+    ST_INIT_POS = 0,
+    ST_INIT_VEL = 1,
+    ST_COLL = 2,
+    ST_COLL_VEL = 3,
+    ST_INJ_A = 4,
+    ST_INJ_B = 5,
+    ST_INJ_N = 6  // number of injections per step (flux rule)
+};
 
 // Device-resident control block: everything a step changes lives here, so a
 // captured graph of one step can be replayed without host involvement.
@@ -36,7 +44,7 @@ struct Ctrl {
     unsigned done_counter;        // finished tiles of the scan kernel
     int removed_total;            // ions removed in the current step
     int ev_step[EV];              // this step's event counts
-    int pad0;
+    int n_cur;                    // ions alive (N; varies with the flux injection rule)
     double Q[MAXD];               // grain charges
     double f_orbit[MAXD][3];      // Eq. 1 force at the last force evaluation
     double wsum[MAXD][REC];       // window sums of the records
@@ -62,7 +70,9 @@ struct Rem {
 
 // Physical constants and run parameters, passed by value to every kernel.
 struct Phys {
-    int N, n_pad, D, flags;
+    int N, n_pad, D, flags;  // N: ions the buffers and plans are sized for (with the flux
+                             // injection rule a capacity above the live count Ctrl::n_cur)
+    double inj_lambda;       // mean injections per step under the flux rule (App. B fluxes)
     double dt, R, H, hz, R2;
     double qm;       // Z e / m_i
     double kdi;      // Z e / (4 pi eps0 m_i): ion acceleration from a grain of charge Q

@@ -70,12 +70,13 @@ __global__ void k_fpos(Phys P, Bufs B, int buf, double ls_inv)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= P.n_pad) return;
-    if (i < P.N) {
+    const int n = B.ctrl->n_cur;  // ions alive
+    if (i < n) {
         const double* X = B.x[buf];
         B.fpos[i] = scaled(P, X[i], X[B.cap + i], X[2 * B.cap + i], ls_inv);
     } else {
         // far-away dummies: 2^-s underflows to zero, so they add nothing
-        const float far = 3.0e4f + 7.0f * (float)(i - P.N);
+        const float far = 3.0e4f + 7.0f * (float)(i - n);
         B.fpos[i] = make_float4(far, far, far, 0.0f);
     }
 }
@@ -370,7 +371,8 @@ __global__ void k_hist(Phys P, Bufs B, unsigned long long* counts, int nr, int n
     const long long step = B.ctrl->step;  // positions after step n live in buffer n & 1
     const double* X = B.x[step & 1];
     const double hz = 0.5 * P.H;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.N; i += gridDim.x * blockDim.x) {
+    const int n = B.ctrl->n_cur;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const double x = X[i], y = X[B.cap + i], z = X[2 * B.cap + i];
         const double r = __dsqrt_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)));
         const int ir = min(max((int)__dmul_rn(r, inv_dr), 0), nr - 1);
