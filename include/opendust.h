@@ -54,6 +54,9 @@ extern "C" {
 #define OD_F_FP32_STATE 32  /* round ion positions and velocities to FP32 after every
                                update (precision study: FP32-only ion state) */
 #define OD_F_NO_GRAPH 64    /* launch each step's kernels directly, not as a CUDA graph */
+#define OD_F_FP64_PAIRS 256 /* study only: ion-ion pair forces in FP64 (one target per thread,
+                                libm exp2/sqrt; ~100x slower) for the precision study of the
+                                FP32 kernels; not with the cutoff, od_tune or a batch */
 #define OD_F_FLUX_INJECT 128 /* inject a Poisson number of ions per step with the mean
                                 n_inf (J_bottom + J_top + J_side) dt / weight of the App. B
                                 fluxes, instead of one per removed ion: N varies (within a

@@ -34,6 +34,7 @@ F_PAPER_SIDE = 16
 F_FP32_STATE = 32
 F_NO_GRAPH = 64
 F_FLUX_INJECT = 128
+F_FP64_PAIRS = 256
 
 Q_GIVEN = 0
 Q_CONSISTENT = 1

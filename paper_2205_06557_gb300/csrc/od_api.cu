@@ -581,16 +581,31 @@ int replan(od_handle* h, int N)
 {
     h->P.N = N;
     if (h->variant < 0 || h->variant >= num_force_variants()) h->variant = default_variant(N);
-    h->F = h->cut_on ? plan_cut(h, N) : plan_forces(N, h->variant, h->sms, h->upb, h->bps);
+    if (h->P.flags & OD_F_FP64_PAIRS) {
+        // one partial slot per ion (the FP64 kernel's): an ordered plan of 128-ion tiles
+        // whose units are the tiles themselves, so every tile has a single slot
+        ForceArgs F{};
+        F.TI = 128;
+        F.n_pad = N == 0 ? 0 : (N + 1023) / 1024 * 1024;
+        F.JC = F.n_pad;
+        F.JS = 1;
+        F.U = F.n_pad / F.TI;
+        F.G = (int)F.U;
+        F.W = 1;
+        h->F = F;
+    } else {
+        h->F = h->cut_on ? plan_cut(h, N) : plan_forces(N, h->variant, h->sms, h->upb, h->bps);
+    }
     h->P.n_pad = h->F.n_pad;
     if (h->F.n_pad > h->npad_cap) return fail(h, OD_EOVERFLOW, "padded ion count exceeds the buffer");
     return ensure_part(h);
 }
 
 // the step's pair-force stage: all pairs (the variant's kernel) or the cutoff's chain
-int launch_pairs(od_handle* h)
+int launch_pairs(od_handle* h, int after_push)
 {
     if (h->cut_on) return launch_forces_cut(h->P, h->B, h->F, h->C, h->cut_grid, h->stream);
+    if (h->P.flags & OD_F_FP64_PAIRS) return launch_forces_f64(h->P, h->B, after_push, h->stream);
     return launch_forces(h->P, h->B, h->F, h->variant, h->stream);
 }
 
@@ -619,7 +634,7 @@ int read_error_word(od_handle* h)
 // forces for the current state (creation or replaced ions)
 int force_eval(od_handle* h)
 {
-    OD_LK(h, launch_pairs(h));
+    OD_LK(h, launch_pairs(h, 0));
     OD_LK(h, launch_kick(h->P, h->B, h->F, 1, h->stream));
     OD_LK(h, launch_dust(h->P, h->B, 1, h->stream));
     return OD_OK;
@@ -636,7 +651,7 @@ int launch_density(od_handle* h)
 int launch_step(od_handle* h)
 {
     OD_LK(h, launch_push_scan(h->P, h->B, h->stream));
-    OD_LK(h, launch_pairs(h));
+    OD_LK(h, launch_pairs(h, 1));
     OD_LK(h, launch_kick(h->P, h->B, h->F, 0, h->stream));
     OD_LK(h, launch_dust(h->P, h->B, 0, h->stream));
     return launch_density(h);
@@ -873,7 +888,7 @@ int od_step(od_handle* h, int64_t n)
                 OD_CK(h, cudaEventRecord(h->ev[0], h->stream));
                 OD_LK(h, launch_push_scan(h->P, h->B, h->stream));
                 OD_CK(h, cudaEventRecord(h->ev[1], h->stream));
-                OD_LK(h, launch_pairs(h));
+                OD_LK(h, launch_pairs(h, 1));
                 OD_CK(h, cudaEventRecord(h->ev[2], h->stream));
                 OD_LK(h, launch_kick(h->P, h->B, h->F, 0, h->stream));
                 OD_CK(h, cudaEventRecord(h->ev[3], h->stream));
@@ -1073,6 +1088,7 @@ int od_set_cutoff(od_handle* h, double r_cut, double r_switch)
     if (!h) return fail(h, OD_EINVAL, "bad handle");
     if (h->batch_member) return fail(h, OD_EINVAL, "the cutoff is set on single runs, not batch members");
     if (h->P.flags & OD_F_FLUX_INJECT) return fail(h, OD_EINVAL, "the cutoff needs a fixed ion count (no flux rule)");
+    if (h->P.flags & OD_F_FP64_PAIRS) return fail(h, OD_EINVAL, "the cutoff runs on the FP32 kernels only");
     if (!std::isfinite(r_cut) || !std::isfinite(r_switch)) return fail(h, OD_EINVAL, "cutoff: non-finite distance");
     OD_CK(h, cudaStreamSynchronize(h->stream));
     int rc;
@@ -1301,6 +1317,7 @@ int od_tune(od_handle* h, int reps, double* ms, int* best_variant, int* best_upb
     if (!h || reps < 1 || h->batch_member)
         return fail(h, OD_EINVAL, "bad handle or repetition count (or a batch member: use od_batch_tune)");
     if (h->cut_on) return fail(h, OD_EINVAL, "the cutoff has a fixed plan: switch it off to tune the all-pairs kernels");
+    if (h->P.flags & OD_F_FP64_PAIRS) return fail(h, OD_EINVAL, "the FP64 study kernel has no variants to tune");
     const int nv = num_force_variants();
     if (ms)
         for (int i = 0; i < nv * 4 * 3; ++i) ms[i] = -1.0;
@@ -1721,6 +1738,8 @@ int od_create_batch(const od_params* ps, int32_t R, od_batch** out)
         if (rc) return bfail(nullptr, rc, "run " + std::to_string(r) + ": " + msg);
         if (ps[r].flags & OD_F_FLUX_INJECT)
             return bfail(nullptr, OD_EINVAL, "run " + std::to_string(r) + ": batched runs keep a fixed ion count");
+        if (ps[r].flags & OD_F_FP64_PAIRS)
+            return bfail(nullptr, OD_EINVAL, "run " + std::to_string(r) + ": the FP64 study kernel runs alone");
     }
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return bfail(nullptr, OD_ENODEV, "no CUDA device");

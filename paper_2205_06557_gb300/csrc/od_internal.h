@@ -170,6 +170,7 @@ int launch_pad(const Phys& P, const Bufs& B, cudaStream_t s);
 int launch_push_scan(const Phys& P, const Bufs& B, cudaStream_t s);
 int launch_forces(const Phys& P, const Bufs& B, const ForceArgs& F, int variant, cudaStream_t s);
 int launch_kick(const Phys& P, const Bufs& B, const ForceArgs& F, int mode, cudaStream_t s);
+int launch_forces_f64(const Phys& P, const Bufs& B, int after_push, cudaStream_t s);
 int launch_dust(const Phys& P, const Bufs& B, int mode, cudaStream_t s);
 int launch_stats(const Phys& P, const Bufs& B, double* mean_se, cudaStream_t s);
 // kind 0: [n][3] -> [3][cap] doubles; 1: [3][cap] -> [n][3]; 2: float4 -> [n][3] doubles;

@@ -259,6 +259,55 @@ int force_blocks_per_sm(int v)
     return nb > 0 ? nb : 1;
 }
 
+// Study-only FP64 pair forces (precision study of the FP32 kernels): one target per
+// thread, sources staged through shared memory, everything in FP64 from the FP64 state
+// (libm exp2 and sqrt), written as partial slot 0 in the scaled units of the FP32
+// kernels: sum_j (1 + s ln2) 2^-s d / s^3 with d = (r_j - r_i) log2(e) / lambda_De.
+// after_push: the step's new positions (the push writes them to the other buffer).
+constexpr int F64_BT = 128;
+
+__global__ void __launch_bounds__(F64_BT) k_forces_f64(Phys P, Bufs B, int after_push, double ls_inv)
+{
+    __shared__ double sx[F64_BT], sy[F64_BT], sz[F64_BT];
+    const long long step = B.ctrl->step;
+    const int buf = after_push ? (int)((step + 1) & 1) : (int)(step & 1);
+    const double* X = B.x[buf];
+    const int n = B.ctrl->n_cur;
+    const long long cap = B.cap;
+    const int i = blockIdx.x * F64_BT + threadIdx.x;
+    const double xi = i < n ? X[i] * ls_inv : 0.0, yi = i < n ? X[cap + i] * ls_inv : 0.0;
+    const double zi = i < n ? X[2 * cap + i] * ls_inv : 0.0;
+    double ax = 0.0, ay = 0.0, az = 0.0;
+    for (int j0 = 0; j0 < n; j0 += F64_BT) {
+        __syncthreads();
+        const int j = j0 + threadIdx.x;
+        sx[threadIdx.x] = j < n ? X[j] * ls_inv : 0.0;
+        sy[threadIdx.x] = j < n ? X[cap + j] * ls_inv : 0.0;
+        sz[threadIdx.x] = j < n ? X[2 * cap + j] * ls_inv : 0.0;
+        __syncthreads();
+        const int jn = min(F64_BT, n - j0);
+        for (int jj = 0; jj < jn; ++jj) {
+            if (j0 + jj == i) continue;
+            const double dx = sx[jj] - xi, dy = sy[jj] - yi, dz = sz[jj] - zi;
+            const double s2 = dx * dx + dy * dy + dz * dz;
+            const double sd = sqrt(s2);
+            const double c = (1.0 + sd * 0.69314718055994531) * exp2(-sd) / (s2 * sd);
+            ax += c * dx;
+            ay += c * dy;
+            az += c * dz;
+        }
+    }
+    if (i < n) B.part[i] = make_float4((float)ax, (float)ay, (float)az, 0.f);
+}
+
+int launch_forces_f64(const Phys& P, const Bufs& B, int after_push, cudaStream_t s)
+{
+    if (P.N == 0 || (P.flags & OD_F_NO_IONION)) return 0;
+    const double ls_inv = 1.4426950408889634 * P.lam_inv;
+    k_forces_f64<<<(P.N + F64_BT - 1) / F64_BT, F64_BT, 0, s>>>(P, B, after_push, ls_inv);
+    return ck(cudaGetLastError());
+}
+
 int launch_forces(const Phys& P, const Bufs& B, const ForceArgs& F, int v, cudaStream_t s)
 {
     if (P.N == 0 || (P.flags & OD_F_NO_IONION) || F.G == 0) return 0;

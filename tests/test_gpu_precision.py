@@ -6,7 +6,10 @@
   the Eq. 1 force on every grain; the errors are printed (PRECISION lines) and bounded;
 * ion state precision: 50 coupled steps of the ~2,000-ion workload with the FP64 ion
   state (default) and with the state rounded to FP32 after every update
-  (OD_F_FP32_STATE); integer events are compared with the oracle step by step.
+  (OD_F_FP32_STATE); integer events are compared with the oracle step by step;
+* the study-only FP64 pair kernel (OD_F_FP64_PAIRS) against the oracle, and long-run
+  grain charge and force of the ~2,000-ion workload with FP32 against FP64 pair forces
+  (window means compared in combined batch-means standard errors).
 """
 import math
 
@@ -99,3 +102,57 @@ def test_ion_state_precision_and_event_parity():
     print("PRECISION tiny 50 steps: FP64 ion state: %d mismatched steps, max |dx| %.2e m; FP32 ion state: %d "
           "mismatched steps, max |dx| %.2e m" % (bad64, dx64, bad32, dx32))
     assert bad64 == 0 and dx64 < 1e-10
+
+
+def _injected(n, flags):
+    p = W.tiny()
+    p.update(n_ions=n, charge_model="given")
+    p["alpha"] = oracle.Oracle(dict(p, n_ions=1)).alpha()
+    o = oracle.Oracle(p)
+    x, v, ids = W.random_ions(n, p["R"], p["H"], seed=77, dust=p["dust"])
+    o.set_ions(x, v, ids)
+    acc_ref, _ = o.forces()
+    run = od.Run(dict(p, flags=flags))
+    run.set_ions(x, v, ids, next_id=n)
+    a = run.get_ions()[2]
+    run.close()
+    return acc_ref, a
+
+
+def test_fp64_study_kernel_is_exact_up_to_the_float_result():
+    """the study-only FP64 pair kernel: what remains is common to both modes (the FP32
+    grain Coulomb term of the kick and the FP32 acceleration), so the medians agree and
+    the largest pair-sum errors of the FP32 kernel disappear"""
+    acc_ref, a64 = _injected(3000, od.F_FP64_PAIRS)
+    _, a32 = _injected(3000, 0)
+    e64 = np.linalg.norm(a64 - acc_ref, axis=1) / np.linalg.norm(acc_ref, axis=1)
+    e32 = np.linalg.norm(a32 - acc_ref, axis=1) / np.linalg.norm(acc_ref, axis=1)
+    print("PRECISION injected 3000 ions: FP64 pair kernel err/|a| max %.2e median %.2e; FP32 kernel max %.2e median "
+          "%.2e" % (e64.max(), np.median(e64), e32.max(), np.median(e32)))
+    assert np.median(e64) < 2e-7 and e64.max() < 0.5 * e32.max()
+
+
+def test_long_run_grain_results_fp32_vs_fp64_pairs():
+    """long-run window means of the grain charge and axial force of the ~2,000-ion
+    workload with FP32 pair forces against the same runs with FP64 pair forces: the
+    trajectories decorrelate, so the means are compared in combined standard errors"""
+    z = []
+    for seed in range(4):
+        res = []
+        for flags in (0, od.F_FP64_PAIRS):
+            p = W.tiny(seed=seed)
+            p["avg_start"] = 1001
+            run = od.Run(dict(p, flags=flags))
+            run.step(5000)
+            mean, se = run.dust_terms()
+            fz = mean[0, 3] + mean[0, 6] + mean[0, 9] + mean[0, 12]
+            sfz = math.sqrt(se[0, 3] ** 2 + se[0, 6] ** 2 + se[0, 9] ** 2 + se[0, 12] ** 2)
+            res.append((mean[0, 0], se[0, 0], fz, sfz))
+            run.close()
+        (q32, sq32, f32, sf32), (q64, sq64, f64, sf64) = res
+        zq = (q32 - q64) / math.hypot(sq32, sq64)
+        zf = (f32 - f64) / math.hypot(sf32, sf64)
+        z += [zq, zf]
+        print("PRECISION long run seed %d (4000-step window): charge FP32 %.6e FP64 %.6e (%.2f SE, rel %.1e); "
+              "F_z FP32 %.4e FP64 %.4e N (%.2f SE)" % (seed, q32, q64, zq, abs(q32 / q64 - 1), f32, f64, zf))
+    assert max(abs(v) for v in z) < 4.0
