@@ -6,6 +6,8 @@
 * 50 coupled steps of the ~2,000-ion workload: every integer event (absorbed per
   grain, outflow, injected per face, collided) bit-exact per step, ion ids identical,
   positions within 1e-10 m, per-step grain records within tolerance;
+* 25 coupled steps of ~19,700 ions with the ordered, symmetric and packed symmetric
+  pair kernels: every integer event and every position as the oracle's;
 * 200 steps: window means of charge and force within 2 combined standard errors;
 * the ~200,000-ion workload in the benchmark's launch configuration: sampled target
   ions and the grain force against the oracle;
@@ -191,6 +193,42 @@ def test_tiny_50_steps_events_bit_exact():
         assert np.all(dv <= 1e-5 * np.linalg.norm(rec_o[:, :, j0:j0 + 3], axis=-1) + 1e-30)
     c = run.counters()
     assert c[13] == 50 and c[14] == o.n_ions
+
+
+_BIG = {}
+
+
+def _big_oracle_run(steps):
+    """~19,700 ions (the ~2,000-ion plasma in a domain 2.14x larger per axis): one oracle
+    run shared by the kernel variants below"""
+    if "o" not in _BIG:
+        p = W.tiny()
+        p.update(R=p["R"] * 2.14, H=p["H"] * 2.14, n_ions=0)
+        p["alpha"] = _alpha(p)
+        o = oracle.Oracle(p)
+        o.step(steps)
+        _BIG.update(p=p, o=o)
+    return _BIG["p"], _BIG["o"]
+
+
+@pytest.mark.parametrize("variant", [None, 9, 15])  # default (ordered), sym<128,4>, sym2<256,4>
+def test_coupled_steps_at_20k_ions_every_kernel(variant):
+    steps = 25
+    p, o = _big_oracle_run(steps)
+    run = od.Run(p)
+    if variant is not None:
+        od.od_set_force_config(run.h, variant, 8, 0)
+    for _ in range(steps):
+        run.step(1)
+    _, ev_o = o.records(1, steps)
+    _, ev_g = run.series(1, steps)
+    bad = np.nonzero((ev_o != ev_g).any(1))[0]
+    assert len(bad) == 0, "first mismatched step %d" % (bad[0] + 1)
+    assert ev_o[:, 8].sum() > 100
+    xo, _, _, ido = o.get_ions()
+    xg, _, _, idg = run.get_ions()
+    assert np.array_equal(ido, idg) and np.abs(xo - xg).max() < 1e-10
+    run.close()
 
 
 def test_tiny_200_steps_long_run_means():
