@@ -220,7 +220,8 @@ int od_kernel_times(od_handle* h, double* ms, int64_t* launches);
  * Variants 0-7 evaluate every ordered pair (threads per block x targets per thread:
  * 64x1, 64x2, 128x2, 128x4, 256x2, 256x4, 128x8, 64x8); variants 8-11 evaluate each
  * unordered pair once and apply it to both ions (Newton's third law; 128x2, 128x4,
- * 256x2, 256x4) and variants 12-15 do the same with packed FP32-pair arithmetic, at the
+ * 256x2, 256x4) and variants 12-18 do the same with packed FP32-pair arithmetic (128x2,
+ * 128x4, 256x2, 256x4, 128x8, 64x8, 32x8), at the
  * price of one partial-sum slot per tile of BT x IPT ions for every ion (device memory
  * N_pad^2 / (BT IPT) x 16 bytes, allocated by the call that selects the variant).  All
  * give forces within FP32 rounding of each other.

@@ -353,7 +353,7 @@ def od_selftest_wait_timeout(h, polls=2000):
 # symmetric kernel on packed FP32 pairs k_forces_sym2
 FORCE_VARIANTS = ((64, 1, 0), (64, 2, 0), (128, 2, 0), (128, 4, 0), (256, 2, 0), (256, 4, 0), (128, 8, 0),
                   (64, 8, 0), (128, 2, 1), (128, 4, 1), (256, 2, 1), (256, 4, 1), (128, 2, 2), (128, 4, 2),
-                  (256, 2, 2), (256, 4, 2))
+                  (256, 2, 2), (256, 4, 2), (128, 8, 2), (64, 8, 2), (32, 8, 2))
 
 
 def force_variant_shape(v):

@@ -219,7 +219,7 @@ int launch_push_scan(const Phys& P, const Bufs& B, cudaStream_t s)
 // the position buffer
 #define OD_FORCE_VARIANTS(X) X(64, 1) X(64, 2) X(128, 2) X(128, 4) X(256, 2) X(256, 4) X(128, 8) X(64, 8)
 #define OD_SYM_VARIANTS(X) X(128, 2) X(128, 4) X(256, 2) X(256, 4)
-#define OD_SYM2_VARIANTS(X) X(128, 2) X(128, 4) X(256, 2) X(256, 4)
+#define OD_SYM2_VARIANTS(X) X(128, 2) X(128, 4) X(256, 2) X(256, 4) X(128, 8) X(64, 8) X(32, 8)
 
 static const ForceVariant kVariants[] = {
 #define OD_V(bt, ipt) {bt, ipt, 0},
