@@ -38,10 +38,11 @@ UNIT = "pairs/s"
 # both ions, i.e. 8.5 FP32 and 1 MUFU per ordered pair.
 PAIRS_PER_CLK_SM = {0: min(128 / 14, 16 / 2), 1: min(128 / 8.5, 16 / 1), 2: min(128 / 8.5, 16 / 1)}
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch, from the full ncu capture of
-# that kernel on that ion count (profiles/k_forces_at_scale_200k.md); any other kernel or
-# size reports null until it has been captured
+# that kernel on that ion count (profiles/k_forces_at_scale_200k.md and
+# profiles/k_forces_sym_at_scale_200k.md); any other kernel or size reports null until it
+# has been captured
 NCU_DRAM_BYTES = {("k_forces<256,2>", 199969): 3217152, ("k_forces_sym2<256,4>", 199969): 574284800,
-                  ("k_forces_sym<128,4>", 199969): 1197502136}
+                  ("k_forces_sym<128,4>", 199969): 1197502136, ("k_forces_sym2<64,8>", 199969): 1200124024}
 
 
 def parse():
