@@ -911,9 +911,11 @@ __device__ __forceinline__ void sym2_unit(const float4* __restrict__ fpos, float
     for (int k = 0; k < IPT; ++k) out[k * BT] = make_float4(ax[k], ay[k], az[k], 0.f);
 }
 
-// Persistent symmetric kernel on packed FP32 pairs: contiguous ranges of tile-pair units
+// Persistent symmetric kernel on packed FP32 pairs: contiguous ranges of tile-pair units.
+// The 8-target variants are held to 128 registers (a few spills) for one more resident
+// CTA per SM, which measured 1% faster than their natural 133.
 template <int BT, int IPT>
-__global__ void __launch_bounds__(BT) k_forces_sym2(const float4* __restrict__ fpos, float4* __restrict__ part,
+__global__ void __launch_bounds__(BT, (IPT == 8 ? 65536 / (BT * 128) : 1)) k_forces_sym2(const float4* __restrict__ fpos, float4* __restrict__ part,
                                                     ForceArgs F)
 {
     __shared__ float s_acc[2][3][BT / 32][SYM_SUB];
