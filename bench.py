@@ -51,7 +51,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="scale", choices=["scale", "tiny", "chain", "sweep", "warmstart", "cutoff"])
+    ap.add_argument("--workload", default="scale",
+                    choices=["scale", "tiny", "chain", "sweep", "warmstart", "cutoff", "production"])
+    ap.add_argument("--run-steps", type=int, default=20000)
     ap.add_argument("--max-all-pairs-log2", type=int, default=20)
     ap.add_argument("--label-steps", type=int, default=60000)
     ap.add_argument("--train-iters", type=int, default=3000)
@@ -486,6 +488,49 @@ def run_cutoff(args):
         print(json.dumps(line), flush=True)
 
 
+def run_production(args):
+    """The ~200,000-ion workload run for --run-steps steps (20,000 by default) with the
+    tuned pair kernel: wall time, ion-steps/s and the grain's time averages (second half)
+    with batch-means standard errors."""
+    import torch
+
+    import paper_2205_06557_gb300 as od
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    p, desc = workload("scale", rank)
+    n_steps = args.run_steps
+    p["avg_start"] = n_steps // 2 + 1
+    run = od.Run(p)
+    tv, tg, tb, _ = od.tune_cached(run.h, "%s|N=%d" % (torch.cuda.get_device_name(local), run.N))
+    q0 = run.dust_now()[0][0]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    done = 0
+    while done < n_steps:
+        k = min(1000, n_steps - done)
+        run.step(k)
+        done += k
+    wall = time.perf_counter() - t0
+    mean, se = run.dust_terms()
+    rec, _ = run.series(n_steps, 1)
+    qe = 1.602176634e-19
+    terms = {"orbit": (1, 4), "grain_grain": (4, 7), "collection": (7, 10), "driving_field": (10, 13)}
+    line = {"metric": "ion-steps/s, production run", "unit": "ion-steps/s", "higher_is_better": True,
+            "value": run.N * n_steps / wall, "n_gpus": 1, "steps": n_steps, "data": "synthetic", "dtype": "f32",
+            "config": {"workload": desc, "n_ions": run.N, "charge_model": "consistent from the OML charge",
+                       "pair_kernel": od.force_variant_name(tv), "window": "steps %d-%d" % (p["avg_start"], n_steps)},
+            "wall_s": wall, "pairs_per_s": float(run.N) * (run.N - 1) * n_steps / wall,
+            "charge_e": {"initial": q0 / qe, "final": rec[0, 0, 0] / qe, "window_mean": mean[0, 0] / qe,
+                         "window_se": se[0, 0] / qe},
+            "force_z_N": {name: {"mean": float(mean[0, a + 2]), "se": float(se[0, a + 2])}
+                          for name, (a, b) in terms.items()},
+            "force_z_total_N": float(sum(mean[0, a + 2] for a, _ in terms.values()))}
+    run.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def ctypes_stream(stream):
     h = stream.cuda_stream
     return h if h else None
@@ -497,6 +542,8 @@ def main():
         run_reference(args)
     elif args.workload == "cutoff":
         run_cutoff(args)
+    elif args.workload == "production":
+        run_production(args)
     elif args.workload == "sweep":
         run_sweep(args)
     elif args.workload == "warmstart":
