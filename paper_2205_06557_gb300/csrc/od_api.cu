@@ -14,21 +14,16 @@
 #include <string>
 #include <vector>
 
-#include "od_internal.h"
+#include "od_host.h"
 
 using namespace od;
+using namespace od::host;
 
-namespace {
-
-// CODATA 2018
-constexpr double kQE = 1.602176634e-19;
-constexpr double kKB = 1.380649e-23;
-constexpr double kEPS0 = 8.8541878128e-12;
-constexpr double kME = 9.1093837015e-31;
-constexpr double kPI = 3.141592653589793238;
-constexpr double kTWO32 = 4294967296.0;
+namespace od {
+namespace host {
 
 thread_local std::string g_create_error;
+
 
 double norm_cdf(double z) { return 0.5 * std::erfc(-z / std::sqrt(2.0)); }
 double norm_pdf(double z) { return std::exp(-0.5 * z * z) / std::sqrt(2.0 * kPI); }
@@ -222,56 +217,13 @@ bool lsq_mgs(int m, int n, std::vector<double> A, std::vector<double> b, double*
     return true;
 }
 
-}  // namespace
+}  // namespace host
+}  // namespace od
 
 void od::set_global_error(const std::string& msg) { g_create_error = msg; }
 
-struct od_handle {
-    Phys P{};
-    Bufs B{};
-    ForceArgs F{};
-    int variant = 0;
-    int upb = 8;  // pair-kernel work units per persistent block
-    int bps = 0;  // persistent pair-kernel CTAs per SM (0 = occupancy limit)
-    bool batch_member = false;  // stepped only through its batch (od_batch_step)
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t gexec = nullptr;
-    bool graph_ok = false;
-    long long cap = 0;       // ion capacity
-    long long npad_cap = 0;  // fpos capacity
-    long long part_cap = 0;  // partial-sum capacity (float4)
-    long long nb_cap = 0;    // kick blocks capacity
-    long long host_step = 0;
-    long long series_cap = 0;
-    int sms = 0;
-    double alpha[15] = {0};
-    double info[32] = {0};
-    std::string err;
-    bool profiling = false;
-    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
-    double kms[4] = {0, 0, 0, 0};
-    long long klaunch[4] = {0, 0, 0, 0};
-    double* d_stats = nullptr;
-    double* d_vtab = nullptr;
-    double* d_series = nullptr;
-    int* d_evseries = nullptr;
-    od_params prm{};                     // creation parameters (pointers cleared): checkpoints
-    od_dust prm_dust[OD_MAX_DUST] = {};
-    unsigned long long* d_hist = nullptr;  // n(r, z) counts [nz][nr] while enabled
-    int hist_nr = 0, hist_nz = 0;
-    long long hist_samples = 0;
-    double* d_io = nullptr;   // device staging of host arrays: x, v, a as [cap][3] each
-    double* h_io = nullptr;   // pinned staging for pageable host arrays (same layout)
-    uint64_t* h_ioid = nullptr;
-    bool cut_on = false;                   // ion-ion cutoff (od_set_cutoff)
-    double r_cut = 0.0, r_switch = 0.0;
-    CutBufs C{};
-    int cut_grid = 1;
-};
-
-namespace {
+namespace od {
+namespace host {
 
 int fail(od_handle* h, int code, const std::string& msg)
 {
@@ -286,17 +238,6 @@ int cuda_fail(od_handle* h, cudaError_t e, const char* where)
                 std::string(where) + ": " + cudaGetErrorString(e));
 }
 
-#define OD_CK(h, call)                                      \
-    do {                                                    \
-        cudaError_t e_ = (call);                            \
-        if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
-    } while (0)
-
-#define OD_LK(h, call)                                                       \
-    do {                                                                     \
-        int e_ = (call);                                                     \
-        if (e_ != 0) return cuda_fail(h, (cudaError_t)e_, #call);            \
-    } while (0)
 
 // parameter checks that need no device
 int validate(const od_params* p, std::string& msg)
@@ -834,7 +775,8 @@ int create_impl(const od_params* p, od_handle* h)
     return read_error_word(h);
 }
 
-}  // namespace
+}  // namespace host
+}  // namespace od
 
 extern "C" {
 
@@ -1083,162 +1025,6 @@ int od_set_ions(od_handle* h, const double* x, const double* v, const double* a,
     return read_error_word(h);
 }
 
-int od_set_cutoff(od_handle* h, double r_cut, double r_switch)
-{
-    if (!h) return fail(h, OD_EINVAL, "bad handle");
-    if (h->batch_member) return fail(h, OD_EINVAL, "the cutoff is set on single runs, not batch members");
-    if (h->P.flags & OD_F_FLUX_INJECT) return fail(h, OD_EINVAL, "the cutoff needs a fixed ion count (no flux rule)");
-    if (h->P.flags & OD_F_FP64_PAIRS) return fail(h, OD_EINVAL, "the cutoff runs on the FP32 kernels only");
-    if (!std::isfinite(r_cut) || !std::isfinite(r_switch)) return fail(h, OD_EINVAL, "cutoff: non-finite distance");
-    OD_CK(h, cudaStreamSynchronize(h->stream));
-    int rc;
-    const int buf = (int)(h->host_step & 1);
-    if (r_cut <= 0.0) {
-        if (!h->cut_on) return OD_OK;
-        h->cut_on = false;
-        h->r_cut = h->r_switch = 0.0;
-        free_cut(h);
-        if ((rc = replan(h, h->P.N))) return rc;
-        h->graph_ok = false;
-        OD_LK(h, launch_fpos(h->P, h->B, buf, h->stream));
-        if ((rc = force_eval(h))) return rc;
-        OD_CK(h, cudaStreamSynchronize(h->stream));
-        return read_error_word(h);
-    }
-    if (!(r_switch >= 0.0 && r_switch < r_cut)) return fail(h, OD_EINVAL, "cutoff: need 0 <= r_switch < r_cut");
-    constexpr int TI = 512;
-    const long long npad_max = (h->cap + TI - 1) / TI * TI;
-    const int T = (int)(npad_max / TI);
-    if (T > CUT_MAX_TILES)
-        return fail(h, OD_EINVAL, "cutoff: at most " + std::to_string(CUT_MAX_TILES * TI) + " ions");
-    // slabs of about an eighth of the cutoff (the slab-by-warp count matrix stays below
-    // 64M entries)
-    const long long nblk = (h->cap + 31) / 32;
-    int nslab = (int)std::min(65536.0, std::max(1.0, std::ceil(h->P.H / (r_cut / 8.0))));
-    while ((long long)nslab * nblk > (64ll << 20) && nslab > 1) nslab = (nslab + 1) / 2;
-    const double w = h->P.H / nslab;
-    // slot capacity: the tiles within the cutoff plus two tile extents, for a uniform
-    // density, with a margin of half again
-    const double ext = 2.0 * std::max(w, h->P.H * TI / std::max(1.0, (double)h->P.N));
-    const double deg = T * std::min(1.0, (2.0 * r_cut + 2.0 * ext) / h->P.H) + 3.0;
-    const int max_deg = (int)std::min<double>(T, std::ceil(1.5 * deg) + 8.0);
-    const double slot_bytes = (double)max_deg * npad_max * sizeof(float4);
-    if (slot_bytes > 48e9)
-        return fail(h, OD_EINVAL, "cutoff: the partial slots would need " + std::to_string(slot_bytes / 1e9) +
-                                      " GB (cutoff too long for this domain)");
-    free_cut(h);
-    CutBufs& C = h->C;
-    const double ls = 1.4426950408889634 * h->P.lam_inv;
-    C.nslab = nslab;
-    C.zoff = (float)(0.5 * h->P.H * ls);
-    C.inv_w = (float)(1.0 / (w * ls));
-    const double rcs = r_cut * ls * (1.0 + 1e-5);  // box test: never drop a pair inside the cutoff
-    C.rc2_tile = (float)(rcs * rcs);
-    const double rss = r_switch * ls * (1.0 - 1e-5);  // plain units: never skip a switched pair
-    C.rs2_tile = (float)(rss * rss);
-    C.max_deg = max_deg;
-    C.err = (int*)((char*)h->B.ctrl + offsetof(Ctrl, err));
-    const long long M = (long long)nslab * nblk;
-    const long long nchunk = (M + 8191) / 8192;
-    OD_CK(h, cudaMalloc(&C.bcount, sizeof(int) * M));
-    OD_CK(h, cudaMalloc(&C.boff, sizeof(int) * M));
-    OD_CK(h, cudaMalloc(&C.bsum, sizeof(int) * nchunk));
-    OD_CK(h, cudaMalloc(&C.perm, sizeof(int) * h->cap));
-    OD_CK(h, cudaMalloc(&C.rank, sizeof(int) * h->cap));
-    OD_CK(h, cudaMalloc(&C.fsort, sizeof(float4) * npad_max));
-    OD_CK(h, cudaMalloc(&C.box_lo, sizeof(float4) * T));
-    OD_CK(h, cudaMalloc(&C.box_hi, sizeof(float4) * T));
-    OD_CK(h, cudaMalloc(&C.nbr_start, sizeof(int) * (T + 1)));
-    OD_CK(h, cudaMalloc(&C.nbr, sizeof(int) * (size_t)T * T));
-    OD_CK(h, cudaMalloc(&C.units, sizeof(int4) * ((size_t)T * (T + 1) / 2)));
-    OD_CK(h, cudaMalloc(&C.n_units, sizeof(int)));
-    OD_CK(h, cudaMalloc(&C.cnt, sizeof(int) * T));
-    OD_CK(h, cudaMalloc(&C.ucnt, sizeof(int) * T));
-    OD_CK(h, cudaMalloc(&C.ustart, sizeof(int) * T));
-    OD_CK(h, cudaMalloc(&C.over, sizeof(int)));
-    h->cut_on = true;
-    h->r_cut = r_cut;
-    h->r_switch = r_switch;
-    h->cut_grid = h->sms * cut_blocks_per_sm(2);
-    if ((rc = replan(h, h->P.N))) return rc;
-    OD_LK(h, launch_cut_dummies(C, h->P.N, h->F.n_pad, h->stream));
-    OD_LK(h, launch_fpos(h->P, h->B, buf, h->stream));
-    h->graph_ok = false;
-    if ((rc = force_eval(h))) return rc;
-    OD_CK(h, cudaStreamSynchronize(h->stream));
-    return read_error_word(h);
-}
-
-int od_density_enable(od_handle* h, int32_t nr, int32_t nz)
-{
-    if (!h || nr < 0 || nz < 0 || nr > 4096 || nz > 4096 || (long long)nr * nz > (1ll << 22) || ((nr == 0) != (nz == 0)))
-        return fail(h, OD_EINVAL, "bad density map size");
-    if (h->batch_member) return fail(h, OD_EINVAL, "density maps are kept for single runs, not batch members");
-    OD_CK(h, cudaStreamSynchronize(h->stream));
-    cudaFree(h->d_hist);
-    h->d_hist = nullptr;
-    h->hist_nr = nr;
-    h->hist_nz = nz;
-    h->hist_samples = 0;
-    h->graph_ok = false;
-    if (nr == 0) return OD_OK;
-    OD_CK(h, cudaMalloc(&h->d_hist, sizeof(unsigned long long) * nr * nz));
-    OD_CK(h, cudaMemsetAsync(h->d_hist, 0, sizeof(unsigned long long) * nr * nz, h->stream));
-    OD_CK(h, cudaStreamSynchronize(h->stream));
-    return OD_OK;
-}
-
-int od_density_read(od_handle* h, uint64_t* counts, double* density, int64_t* samples)
-{
-    if (!h) return fail(h, OD_EINVAL, "bad handle");
-    if (!h->d_hist) return fail(h, OD_EINVAL, "no density map: call od_density_enable first");
-    const int nr = h->hist_nr, nz = h->hist_nz;
-    std::vector<unsigned long long> c((size_t)nr * nz);
-    OD_CK(h, cudaMemcpyAsync(c.data(), h->d_hist, sizeof(unsigned long long) * c.size(), cudaMemcpyDeviceToHost,
-                             h->stream));
-    OD_CK(h, cudaStreamSynchronize(h->stream));
-    if (counts) std::memcpy(counts, c.data(), sizeof(uint64_t) * c.size());
-    if (samples) *samples = h->hist_samples;
-    if (density) {
-        const double R = h->P.R, dz = h->P.H / nz, w = h->prm.weight > 0 ? h->prm.weight : 1.0;
-        for (int iz = 0; iz < nz; ++iz)
-            for (int ir = 0; ir < nr; ++ir) {
-                const double r0 = R * ir / nr, r1 = R * (ir + 1) / nr;
-                const double vol = 3.141592653589793 * (r1 * r1 - r0 * r0) * dz;
-                density[(size_t)iz * nr + ir] =
-                    h->hist_samples > 0 ? (double)c[(size_t)iz * nr + ir] * w / (h->hist_samples * vol) : 0.0;
-            }
-    }
-    return OD_OK;
-}
-
-int od_write_ions(od_handle* h, const char* path, int32_t format)
-{
-    if (!h || !path || (format != OD_DUMP_XYZ && format != OD_DUMP_CSV)) return fail(h, OD_EINVAL, "bad argument");
-    const long long N = h->P.N;
-    std::vector<double> x(3 * (size_t)std::max(N, 1ll)), v(x.size());
-    std::vector<uint64_t> id((size_t)std::max(N, 1ll));
-    const int64_t got = od_get_ions(h, x.data(), v.data(), nullptr, id.data(), N);
-    if (got < 0) return (int)got;
-    FILE* f = std::fopen(path, "w");
-    if (!f) return fail(h, OD_EINVAL, std::string("cannot open ") + path);
-    if (format == OD_DUMP_XYZ) {
-        std::fprintf(f, "%lld\n", N);
-        std::fprintf(f, "Properties=species:S:1:pos:R:3:vel:R:3:id:I:1 step=%lld time=%.17g units=SI\n", h->host_step,
-                     h->host_step * h->P.dt);
-        for (long long i = 0; i < N; ++i)
-            std::fprintf(f, "I %.17g %.17g %.17g %.17g %.17g %.17g %llu\n", x[3 * i], x[3 * i + 1], x[3 * i + 2],
-                         v[3 * i], v[3 * i + 1], v[3 * i + 2], (unsigned long long)id[i]);
-    } else {
-        std::fprintf(f, "id,x,y,z,vx,vy,vz\n");
-        for (long long i = 0; i < N; ++i)
-            std::fprintf(f, "%llu,%.17g,%.17g,%.17g,%.17g,%.17g,%.17g\n", (unsigned long long)id[i], x[3 * i],
-                         x[3 * i + 1], x[3 * i + 2], v[3 * i], v[3 * i + 1], v[3 * i + 2]);
-    }
-    const bool ok = std::fclose(f) == 0;
-    return ok ? OD_OK : fail(h, OD_EINVAL, std::string("write failed: ") + path);
-}
-
 int od_info(od_handle* h, double* out)
 {
     if (!h || !out) return fail(h, OD_EINVAL, "bad argument");
@@ -1285,108 +1071,6 @@ int od_oml_charge(const od_params* p, double radius, double* Q)
     return OD_OK;
 }
 
-static const int kTuneGrains[4] = {4, 8, 16, 32};
-static const int kTuneBps[3] = {0, 4, 2};  // persistent CTAs per SM: 0 = occupancy limit
-
-static int apply_force_config(od_handle* h, int variant, int upb, int bps)
-{
-    h->variant = variant;
-    h->upb = upb;
-    h->bps = bps;
-    int rc = replan(h, h->P.N);
-    if (rc) return rc;
-    h->graph_ok = false;
-    // the padded length may have grown: rewrite positions and far-away dummies
-    OD_LK(h, launch_fpos(h->P, h->B, (int)(h->host_step & 1), h->stream));
-    return OD_OK;
-}
-
-int od_set_force_config(od_handle* h, int variant, int units_per_block, int blocks_per_sm)
-{
-    if (!h || variant < 0 || variant >= num_force_variants() || units_per_block < 1 || units_per_block > 1024 ||
-        blocks_per_sm < 0 || blocks_per_sm > 64 || h->batch_member)
-        return fail(h, OD_EINVAL, "bad force configuration (or a batch member: use od_batch_set_config)");
-    int rc = apply_force_config(h, variant, units_per_block, blocks_per_sm);
-    if (rc) return rc;
-    OD_CK(h, cudaStreamSynchronize(h->stream));
-    return OD_OK;
-}
-
-int od_tune(od_handle* h, int reps, double* ms, int* best_variant, int* best_upb, int* best_bps)
-{
-    if (!h || reps < 1 || h->batch_member)
-        return fail(h, OD_EINVAL, "bad handle or repetition count (or a batch member: use od_batch_tune)");
-    if (h->cut_on) return fail(h, OD_EINVAL, "the cutoff has a fixed plan: switch it off to tune the all-pairs kernels");
-    if (h->P.flags & OD_F_FP64_PAIRS) return fail(h, OD_EINVAL, "the FP64 study kernel has no variants to tune");
-    const int nv = num_force_variants();
-    if (ms)
-        for (int i = 0; i < nv * 4 * 3; ++i) ms[i] = -1.0;
-    if (h->P.N == 0 || (h->P.flags & OD_F_NO_IONION)) {
-        if (best_variant) *best_variant = h->variant;
-        if (best_upb) *best_upb = h->upb;
-        if (best_bps) *best_bps = h->bps;
-        return OD_OK;
-    }
-    double best = 1e300;
-    int bv = h->variant, bg = h->upb, bb = h->bps;
-    size_t free_b = 0, total_b = 0;
-    OD_CK(h, cudaMemGetInfo(&free_b, &total_b));
-    const double slot_budget = (double)(free_b + sizeof(float4) * (size_t)h->part_cap) / 8.0;
-    for (int v = 0; v < nv; ++v)
-        for (int g = 0; g < 4; ++g)
-            for (int c = 0; c < 3; ++c) {
-                if (kTuneBps[c] >= force_blocks_per_sm(v)) continue;  // no cap below the occupancy limit
-                const ForceVariant fv = force_variant(v);
-                if (fv.sym) {
-                    if (g > 0) continue;  // fixed-size units: one grain setting
-                    // one partial slot per tile for every ion: skip layouts that would take
-                    // more than an eighth of the device memory
-                    const double ti = fv.BT * fv.IPT, np = std::ceil(h->P.N / ti) * ti;
-                    if (np / ti * np * sizeof(float4) > slot_budget) continue;
-                }
-                int rc = apply_force_config(h, v, kTuneGrains[g], kTuneBps[c]);
-                if (rc) return rc;
-                // the kick is timed too: it sums every ion's partial slots, one per tile
-                // for the symmetric kernel
-                OD_LK(h, launch_forces(h->P, h->B, h->F, h->variant, h->stream));
-                OD_CK(h, cudaEventRecord(h->ev[0], h->stream));
-                for (int r = 0; r < reps; ++r) {
-                    OD_LK(h, launch_forces(h->P, h->B, h->F, h->variant, h->stream));
-                    OD_LK(h, launch_kick(h->P, h->B, h->F, 1, h->stream));
-                }
-                OD_CK(h, cudaEventRecord(h->ev[1], h->stream));
-                OD_CK(h, cudaEventSynchronize(h->ev[1]));
-                float t = 0.f;
-                OD_CK(h, cudaEventElapsedTime(&t, h->ev[0], h->ev[1]));
-                const double avg = t / reps;
-                if (ms) ms[(v * 4 + g) * 3 + c] = avg;
-                if (avg < best) {
-                    best = avg;
-                    bv = v;
-                    bg = kTuneGrains[g];
-                    bb = kTuneBps[c];
-                }
-            }
-    int rc = apply_force_config(h, bv, bg, bb);
-    if (rc) return rc;
-    // give back partial-slot memory beyond what the chosen layout needs
-    if (h->part_cap > 2 * (long long)h->F.W * h->F.n_pad) {
-        OD_CK(h, cudaStreamSynchronize(h->stream));
-        cudaFree(h->B.part);
-        h->B.part = nullptr;
-        h->part_cap = 0;
-        if ((rc = ensure_part(h))) return rc;
-    }
-    // the accelerations and partial sums left by the timing belong to other kernels:
-    // evaluate the current state again with the chosen one
-    if ((rc = force_eval(h))) return rc;
-    OD_CK(h, cudaStreamSynchronize(h->stream));
-    if (best_variant) *best_variant = bv;
-    if (best_upb) *best_upb = bg;
-    if (best_bps) *best_bps = bb;
-    return read_error_word(h);
-}
-
 int od_selftest_wait_timeout(od_handle* h, int64_t polls)
 {
     if (!h || polls < 1) return fail(h, OD_EINVAL, "bad handle or poll limit");
@@ -1400,511 +1084,7 @@ int od_selftest_wait_timeout(od_handle* h, int64_t polls)
     return read_error_word(h);
 }
 
-int od_get_force_config(od_handle* h, int* variant, int* units_per_block, int* blocks_per_sm, int* n_variants)
-{
-    if (!h) return fail(h, OD_EINVAL, "bad handle");
-    if (variant) *variant = h->variant;
-    if (units_per_block) *units_per_block = h->upb;
-    if (blocks_per_sm) *blocks_per_sm = h->bps;
-    if (n_variants) *n_variants = num_force_variants();
-    return OD_OK;
-}
-
 int od_num_dust(od_handle* h) { return h ? h->P.D : fail(h, OD_EINVAL, "bad handle"); }
 
-// ------------------------------------------------------------------ checkpoints
-// File layout (host byte order): CkptHeader, then x[N][3], v[N][3] (double), id[N]
-// (uint64), acc[N] (float x4), the control block (ctrl_bytes), the per-step records
-// double[n_series][OD_MAX_DUST][OD_REC] and events int32[n_series][OD_EV].
-struct CkptHeader {
-    char magic[8];
-    uint32_t version, header_bytes;
-    double ion_mass, ion_charge_number, T_i, T_n, T_e, n_inf, mach, E_ext, nu_in, R, H, dt, weight;
-    int64_t n_ions;
-    int32_t n_dust, charge_model;
-    uint64_t seed;
-    int64_t avg_start;
-    int32_t flags, eout_grid;
-    od_dust dust[OD_MAX_DUST];
-    double alpha[15];
-    int64_t N, step;
-    int32_t variant, upb, bps, pad;
-    int64_t n_series;
-    uint64_t ctrl_bytes;
-    double r_cut, r_switch;  // ion-ion cutoff (0: none)
-};
-static const char kCkptMagic[8] = {'O', 'D', 'C', 'K', 'P', 'T', '0', '1'};
-
-int od_save(od_handle* h, const char* path)
-{
-    if (!h || !path) return fail(h, OD_EINVAL, "bad argument");
-    if (h->batch_member) return fail(h, OD_EINVAL, "batch members are saved through their own runs' state only");
-    const long long N = h->P.N;
-    CkptHeader hd{};
-    std::memcpy(hd.magic, kCkptMagic, 8);
-    hd.version = 1;
-    hd.header_bytes = sizeof(CkptHeader);
-    const od_params& p = h->prm;
-    hd.ion_mass = p.ion_mass, hd.ion_charge_number = p.ion_charge_number, hd.T_i = p.T_i, hd.T_n = p.T_n;
-    hd.T_e = p.T_e, hd.n_inf = p.n_inf, hd.mach = p.mach, hd.E_ext = p.E_ext, hd.nu_in = p.nu_in;
-    hd.R = p.R, hd.H = p.H, hd.dt = p.dt, hd.weight = p.weight, hd.n_ions = p.n_ions;
-    hd.n_dust = p.n_dust, hd.charge_model = p.charge_model, hd.seed = p.seed, hd.avg_start = p.avg_start;
-    hd.flags = p.flags, hd.eout_grid = p.eout_grid;
-    for (int k = 0; k < p.n_dust; ++k) hd.dust[k] = h->prm_dust[k];
-    for (int t = 0; t < 15; ++t) hd.alpha[t] = h->alpha[t];
-    hd.N = N;
-    hd.step = h->host_step;
-    hd.variant = h->variant, hd.upb = h->upb, hd.bps = h->bps;
-    hd.n_series = std::min<long long>(h->host_step, h->series_cap);
-    hd.ctrl_bytes = sizeof(Ctrl);
-    hd.r_cut = h->cut_on ? h->r_cut : 0.0;
-    hd.r_switch = h->cut_on ? h->r_switch : 0.0;
-    std::vector<double> x(3 * (size_t)std::max(N, 1ll)), v(x.size());
-    std::vector<uint64_t> id((size_t)std::max(N, 1ll));
-    const int64_t got = od_get_ions(h, x.data(), v.data(), nullptr, id.data(), N);
-    if (got < 0) return (int)got;
-    std::vector<float4> acc((size_t)std::max(N, 1ll));
-    Ctrl c;
-    std::vector<double> ser((size_t)hd.n_series * MAXD * REC);
-    std::vector<int> evs((size_t)hd.n_series * EV);
-    if (N > 0) OD_CK(h, cudaMemcpyAsync(acc.data(), h->B.acc, sizeof(float4) * N, cudaMemcpyDeviceToHost, h->stream));
-    OD_CK(h, cudaMemcpyAsync(&c, h->B.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
-    if (hd.n_series > 0) {
-        OD_CK(h, cudaMemcpyAsync(ser.data(), h->d_series, sizeof(double) * ser.size(), cudaMemcpyDeviceToHost, h->stream));
-        OD_CK(h, cudaMemcpyAsync(evs.data(), h->d_evseries, sizeof(int) * evs.size(), cudaMemcpyDeviceToHost, h->stream));
-    }
-    OD_CK(h, cudaStreamSynchronize(h->stream));
-    c.series = nullptr;  // device addresses mean nothing in a file
-    c.evseries = nullptr;
-    FILE* f = std::fopen(path, "wb");
-    if (!f) return fail(h, OD_EINVAL, std::string("cannot open ") + path);
-    bool ok = std::fwrite(&hd, sizeof(hd), 1, f) == 1;
-    ok = ok && (N == 0 || (std::fwrite(x.data(), sizeof(double), 3 * N, f) == (size_t)(3 * N) &&
-                           std::fwrite(v.data(), sizeof(double), 3 * N, f) == (size_t)(3 * N) &&
-                           std::fwrite(id.data(), sizeof(uint64_t), N, f) == (size_t)N &&
-                           std::fwrite(acc.data(), sizeof(float4), N, f) == (size_t)N));
-    ok = ok && std::fwrite(&c, sizeof(Ctrl), 1, f) == 1;
-    ok = ok && (ser.empty() || std::fwrite(ser.data(), sizeof(double), ser.size(), f) == ser.size());
-    ok = ok && (evs.empty() || std::fwrite(evs.data(), sizeof(int), evs.size(), f) == evs.size());
-    ok = (std::fclose(f) == 0) && ok;
-    return ok ? OD_OK : fail(h, OD_EINVAL, std::string("write failed: ") + path);
-}
-
-int od_load(const char* path, void* cuda_stream, od_handle** out)
-{
-    if (!out || !path) return fail(nullptr, OD_EINVAL, "bad argument");
-    *out = nullptr;
-    FILE* f = std::fopen(path, "rb");
-    if (!f) return fail(nullptr, OD_EINVAL, std::string("cannot open ") + path);
-    CkptHeader hd{};
-    auto bad = [&](const std::string& m) {
-        std::fclose(f);
-        return fail(nullptr, OD_EINVAL, "not a checkpoint of this library (" + m + "): " + path);
-    };
-    if (std::fread(&hd, sizeof(hd), 1, f) != 1) return bad("short header");
-    if (std::memcmp(hd.magic, kCkptMagic, 8) != 0) return bad("magic");
-    if (hd.version != 1 || hd.header_bytes != sizeof(CkptHeader) || hd.ctrl_bytes != sizeof(Ctrl))
-        return bad("version or layout");
-    if (hd.N < 0 || hd.step < 0 || hd.n_series < 0 || hd.n_series > hd.step || hd.n_dust < 0 || hd.n_dust > OD_MAX_DUST)
-        return bad("sizes");
-    const long long N = hd.N;
-    std::vector<double> x(3 * (size_t)std::max(N, 1ll)), v(x.size());
-    std::vector<uint64_t> id((size_t)std::max(N, 1ll));
-    std::vector<float4> acc((size_t)std::max(N, 1ll));
-    Ctrl c;
-    std::vector<double> ser((size_t)hd.n_series * MAXD * REC);
-    std::vector<int> evs((size_t)hd.n_series * EV);
-    bool ok = N == 0 || (std::fread(x.data(), sizeof(double), 3 * N, f) == (size_t)(3 * N) &&
-                         std::fread(v.data(), sizeof(double), 3 * N, f) == (size_t)(3 * N) &&
-                         std::fread(id.data(), sizeof(uint64_t), N, f) == (size_t)N &&
-                         std::fread(acc.data(), sizeof(float4), N, f) == (size_t)N);
-    ok = ok && std::fread(&c, sizeof(Ctrl), 1, f) == 1;
-    ok = ok && (ser.empty() || std::fread(ser.data(), sizeof(double), ser.size(), f) == ser.size());
-    ok = ok && (evs.empty() || std::fread(evs.data(), sizeof(int), evs.size(), f) == evs.size());
-    if (!ok) return bad("truncated");
-    std::fclose(f);
-    if (c.step != hd.step) return fail(nullptr, OD_EINVAL, std::string("inconsistent checkpoint: ") + path);
-    od_params p{};
-    p.ion_mass = hd.ion_mass, p.ion_charge_number = hd.ion_charge_number, p.T_i = hd.T_i, p.T_n = hd.T_n;
-    p.T_e = hd.T_e, p.n_inf = hd.n_inf, p.mach = hd.mach, p.E_ext = hd.E_ext, p.nu_in = hd.nu_in;
-    p.R = hd.R, p.H = hd.H, p.dt = hd.dt, p.weight = hd.weight;
-    p.n_ions = N > 0 ? N : hd.n_ions;
-    p.n_dust = hd.n_dust, p.charge_model = hd.charge_model, p.dust = hd.dust, p.seed = hd.seed;
-    p.avg_start = hd.avg_start, p.eout_coeffs = hd.alpha, p.flags = hd.flags, p.eout_grid = hd.eout_grid;
-    p.cuda_stream = cuda_stream;
-    od_handle* h = nullptr;
-    int rc = od_create(&p, &h);
-    if (rc) return rc;
-    auto done = [&](int code) {
-        if (code) {
-            g_create_error = h->err;
-            od_destroy(h);
-        } else {
-            *out = h;
-        }
-        return code;
-    };
-    // the creation parameters as saved (n_ions as given originally)
-    h->prm.n_ions = hd.n_ions;
-    if (hd.r_cut > 0.0 && (rc = od_set_cutoff(h, hd.r_cut, hd.r_switch))) return done(rc);
-    h->host_step = hd.step;
-    const int buf = (int)(hd.step & 1);
-    if (N > 0) {
-        std::vector<double> tmp(3 * (size_t)N);
-        for (int which = 0; which < 2; ++which) {
-            const double* src = which == 0 ? x.data() : v.data();
-            double* d = which == 0 ? h->B.x[buf] : h->B.v[buf];
-            for (long long i = 0; i < N; ++i)
-                for (int k = 0; k < 3; ++k) tmp[k * N + i] = src[3 * i + k];
-            for (int k = 0; k < 3; ++k)
-                if (cudaMemcpyAsync(d + k * h->cap, tmp.data() + k * N, sizeof(double) * N, cudaMemcpyHostToDevice,
-                                    h->stream) != cudaSuccess)
-                    return done(fail(h, OD_ECUDA, "checkpoint upload failed"));
-            if (cudaStreamSynchronize(h->stream) != cudaSuccess) return done(fail(h, OD_ECUDA, "checkpoint upload failed"));
-        }
-        if (cudaMemcpyAsync(h->B.id[buf], id.data(), sizeof(uint64_t) * N, cudaMemcpyHostToDevice, h->stream) !=
-                cudaSuccess ||
-            cudaMemcpyAsync(h->B.acc, acc.data(), sizeof(float4) * N, cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
-            return done(fail(h, OD_ECUDA, "checkpoint upload failed"));
-    }
-    if ((rc = ensure_series(h, std::max<long long>(hd.n_series, 1)))) return done(rc);
-    if (hd.n_series > 0 &&
-        (cudaMemcpyAsync(h->d_series, ser.data(), sizeof(double) * ser.size(), cudaMemcpyHostToDevice, h->stream) !=
-             cudaSuccess ||
-         cudaMemcpyAsync(h->d_evseries, evs.data(), sizeof(int) * evs.size(), cudaMemcpyHostToDevice, h->stream) !=
-             cudaSuccess))
-        return done(fail(h, OD_ECUDA, "checkpoint upload failed"));
-    c.series = h->d_series;
-    c.evseries = h->d_evseries;
-    c.series_cap = h->series_cap;
-    if (cudaMemcpyAsync(h->B.ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
-        return done(fail(h, OD_ECUDA, "checkpoint upload failed"));
-    // the pair kernel that produced the saved state, so that the continuation is exact
-    if (hd.variant >= 0 && hd.variant < num_force_variants()) {
-        if ((rc = apply_force_config(h, hd.variant, hd.upb, hd.bps))) return done(rc);
-    } else {
-        if ((rc = replan(h, plan_n(h, N)))) return done(rc);
-        if (launch_fpos(h->P, h->B, buf, h->stream)) return done(fail(h, OD_ECUDA, "position refresh failed"));
-    }
-    h->graph_ok = false;
-    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return done(fail(h, OD_ECUDA, "checkpoint upload failed"));
-    return done(read_error_word(h));
-}
-
-}  // extern "C"
-
-// ------------------------------------------------------------------ batches
-struct od_batch {
-    std::vector<od_handle*> runs;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    RunDesc* d_runs = nullptr;
-    int2* d_tasks = nullptr;
-    int2* d_tasks_f = nullptr;          // tuning: pair units, then kick tiles
-    unsigned long long* d_done = nullptr;
-    unsigned long long* d_done_f = nullptr;  // phase counters of the tuning launches
-    BatchCtrl* d_bc = nullptr;
-    BatchCtrl* d_bc_f = nullptr;
-    long long T = 0, T_f = 0;
-    int4 phase_end{0, 0, 0, 0}, phase_end_f{0, 0, 0, 0};
-    int ipt = 2, jc = 4096, grid = 1, sms = 1;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t gexec = nullptr;
-    bool graph_ok = false;
-    long long host_step = 0;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    std::string err;
-};
-
-namespace {
-
-thread_local std::string g_batch_error;
-
-int bfail(od_batch* b, int code, const std::string& msg)
-{
-    if (b) b->err = msg;
-    else g_batch_error = msg;
-    return code;
-}
-
-#define OD_BCK(b, call)                                                                              \
-    do {                                                                                             \
-        cudaError_t e_ = (call);                                                                     \
-        if (e_ != cudaSuccess)                                                                       \
-            return bfail(b, e_ == cudaErrorMemoryAllocation ? OD_ENOMEM : OD_ECUDA,                  \
-                         std::string(#call) + ": " + cudaGetErrorString(e_));                        \
-    } while (0)
-
-// apply the batch pair plan (ipt, jc) to every run and rebuild the task lists
-int batch_build(od_batch* b)
-{
-    const int R = (int)b->runs.size();
-    std::vector<RunDesc> desc(R);
-    std::vector<int2> tA, tF, tK, tD;
-    for (int r = 0; r < R; ++r) {
-        od_handle* h = b->runs[r];
-        h->F = batch_plan(h->P.N, b->ipt, b->jc);
-        h->P.n_pad = h->F.n_pad;
-        if (h->F.n_pad > h->npad_cap) return bfail(b, OD_EOVERFLOW, "padded ion count exceeds a run's buffer");
-        int rc = ensure_part(h);
-        if (rc) return bfail(b, rc, h->err);
-        rc = launch_fpos(h->P, h->B, (int)(h->host_step & 1), b->stream);
-        if (rc) return bfail(b, OD_ECUDA, "batch: position refresh failed");
-        desc[r].P = h->P;
-        desc[r].B = h->B;
-        desc[r].F = h->F;
-        desc[r].nA = (h->P.N + BATCH_TILE - 1) / BATCH_TILE;
-        desc[r].nK = desc[r].nA;
-        for (int i = 0; i < desc[r].nA; ++i) tA.push_back(make_int2(r, i));
-        for (long long u = 0; u < h->F.U; ++u) tF.push_back(make_int2(r, (int)u));
-        for (int i = 0; i < desc[r].nK; ++i) tK.push_back(make_int2(r, i));
-        tD.push_back(make_int2(r, 0));
-    }
-    std::vector<int2> all;
-    all.insert(all.end(), tA.begin(), tA.end());
-    all.insert(all.end(), tF.begin(), tF.end());
-    all.insert(all.end(), tK.begin(), tK.end());
-    all.insert(all.end(), tD.begin(), tD.end());
-    b->phase_end = make_int4((int)tA.size(), (int)(tA.size() + tF.size()), (int)(tA.size() + tF.size() + tK.size()),
-                             (int)all.size());
-    b->T = (long long)all.size();
-    std::vector<int2> fk(tF);
-    fk.insert(fk.end(), tK.begin(), tK.end());
-    b->phase_end_f = make_int4(0, (int)tF.size(), (int)fk.size(), (int)fk.size());
-    b->T_f = (long long)fk.size();
-    cudaFree(b->d_runs);
-    cudaFree(b->d_tasks);
-    cudaFree(b->d_tasks_f);
-    b->d_runs = nullptr;
-    b->d_tasks = b->d_tasks_f = nullptr;
-    OD_BCK(b, cudaMalloc(&b->d_runs, sizeof(RunDesc) * R));
-    OD_BCK(b, cudaMalloc(&b->d_tasks, sizeof(int2) * std::max<size_t>(all.size(), 1)));
-    OD_BCK(b, cudaMalloc(&b->d_tasks_f, sizeof(int2) * std::max<size_t>(fk.size(), 1)));
-    OD_BCK(b, cudaMemcpyAsync(b->d_runs, desc.data(), sizeof(RunDesc) * R, cudaMemcpyHostToDevice, b->stream));
-    OD_BCK(b, cudaMemcpyAsync(b->d_tasks, all.data(), sizeof(int2) * all.size(), cudaMemcpyHostToDevice, b->stream));
-    if (!fk.empty())
-        OD_BCK(b, cudaMemcpyAsync(b->d_tasks_f, fk.data(), sizeof(int2) * fk.size(), cudaMemcpyHostToDevice, b->stream));
-    b->grid = (int)std::max(1ll, std::min<long long>((long long)batch_blocks_per_sm(b->ipt) * b->sms, b->T));
-    OD_BCK(b, cudaStreamSynchronize(b->stream));
-    b->graph_ok = false;
-    return OD_OK;
-}
-
-void batch_free(od_batch* b)
-{
-    if (b->stream) cudaStreamSynchronize(b->stream);
-    for (od_handle* h : b->runs) {
-        free_all(h);
-        delete h;
-    }
-    cudaFree(b->d_runs);
-    cudaFree(b->d_tasks);
-    cudaFree(b->d_tasks_f);
-    cudaFree(b->d_done);
-    cudaFree(b->d_done_f);
-    cudaFree(b->d_bc);
-    cudaFree(b->d_bc_f);
-    if (b->gexec) cudaGraphExecDestroy(b->gexec);
-    if (b->graph) cudaGraphDestroy(b->graph);
-    if (b->e0) cudaEventDestroy(b->e0);
-    if (b->e1) cudaEventDestroy(b->e1);
-    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
-}
-
-int batch_check(od_batch* b)
-{
-    BatchCtrl bc;
-    OD_BCK(b, cudaMemcpyAsync(&bc, b->d_bc, sizeof(bc), cudaMemcpyDeviceToHost, b->stream));
-    OD_BCK(b, cudaStreamSynchronize(b->stream));
-    if (bc.err & ERR_TIMEOUT) return bfail(b, OD_ETIMEOUT, "batch: a task's dependency wait hit its limit");
-    for (size_t r = 0; r < b->runs.size(); ++r) {
-        const int rc = read_error_word(b->runs[r]);
-        if (rc) return bfail(b, rc, "run " + std::to_string(r) + ": " + b->runs[r]->err);
-    }
-    return OD_OK;
-}
-
-}  // namespace
-
-extern "C" {
-
-int od_create_batch(const od_params* ps, int32_t R, od_batch** out)
-{
-    if (!out || !ps || R < 1) return bfail(nullptr, OD_EINVAL, "bad batch arguments");
-    *out = nullptr;
-    for (int r = 0; r < R; ++r) {
-        std::string msg;
-        const int rc = validate(ps + r, msg);
-        if (rc) return bfail(nullptr, rc, "run " + std::to_string(r) + ": " + msg);
-        if (ps[r].flags & OD_F_FLUX_INJECT)
-            return bfail(nullptr, OD_EINVAL, "run " + std::to_string(r) + ": batched runs keep a fixed ion count");
-        if (ps[r].flags & OD_F_FP64_PAIRS)
-            return bfail(nullptr, OD_EINVAL, "run " + std::to_string(r) + ": the FP64 study kernel runs alone");
-    }
-    int ndev = 0;
-    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return bfail(nullptr, OD_ENODEV, "no CUDA device");
-    od_batch* b = new od_batch();
-    int rc = OD_OK;
-    auto fail_out = [&](int code) {
-        g_batch_error = b->err;
-        batch_free(b);
-        delete b;
-        return code;
-    };
-    if (ps[0].cuda_stream) {
-        b->stream = (cudaStream_t)ps[0].cuda_stream;
-    } else if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
-        b->err = "stream creation failed";
-        return fail_out(OD_ECUDA);
-    } else {
-        b->own_stream = true;
-    }
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
-    for (int r = 0; r < R; ++r) {
-        od_params p = ps[r];
-        p.cuda_stream = b->stream;
-        od_handle* h = new od_handle();
-        h->batch_member = true;
-        rc = create_impl(&p, h);
-        if (rc) {
-            b->err = "run " + std::to_string(r) + ": " + h->err;
-            free_all(h);
-            delete h;
-            return fail_out(rc);
-        }
-        h->batch_member = true;
-        h->own_stream = false;
-        b->runs.push_back(h);
-    }
-    if (cudaMalloc(&b->d_done, sizeof(unsigned long long) * 3 * R) != cudaSuccess ||
-        cudaMalloc(&b->d_done_f, sizeof(unsigned long long) * 3 * R) != cudaSuccess ||
-        cudaMalloc(&b->d_bc, sizeof(BatchCtrl)) != cudaSuccess || cudaMalloc(&b->d_bc_f, sizeof(BatchCtrl)) != cudaSuccess ||
-        cudaEventCreate(&b->e0) != cudaSuccess || cudaEventCreate(&b->e1) != cudaSuccess) {
-        b->err = "batch allocation failed";
-        return fail_out(OD_ENOMEM);
-    }
-    cudaMemsetAsync(b->d_done, 0, sizeof(unsigned long long) * 3 * R, b->stream);
-    cudaMemsetAsync(b->d_bc, 0, sizeof(BatchCtrl), b->stream);
-    rc = batch_build(b);
-    if (rc) return fail_out(rc);
-    *out = b;
-    return OD_OK;
-}
-
-int od_batch_step(od_batch* b, int64_t n)
-{
-    if (!b || n < 0) return bfail(b, OD_EINVAL, "bad batch or step count");
-    if (n == 0) return OD_OK;
-    for (od_handle* h : b->runs) {
-        const int rc = ensure_series(h, h->host_step + n);
-        if (rc) return bfail(b, rc, h->err);
-    }
-    if (!b->graph_ok) {
-        if (b->gexec) cudaGraphExecDestroy(b->gexec);
-        if (b->graph) cudaGraphDestroy(b->graph);
-        b->gexec = nullptr;
-        b->graph = nullptr;
-        OD_BCK(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-        const int lrc = launch_batch(b->ipt, b->grid, b->d_runs, b->d_tasks, b->phase_end, b->T, b->d_bc, b->d_done,
-                                     (int)b->runs.size(), SPIN_LIMIT, 0, b->stream);
-        cudaGraph_t g = nullptr;
-        const cudaError_t e = cudaStreamEndCapture(b->stream, &g);
-        if (lrc) return bfail(b, OD_ECUDA, std::string("batch launch: ") + cudaGetErrorString((cudaError_t)lrc));
-        if (e != cudaSuccess) return bfail(b, OD_ECUDA, std::string("batch capture: ") + cudaGetErrorString(e));
-        b->graph = g;
-        OD_BCK(b, cudaGraphInstantiate(&b->gexec, g, 0));
-        b->graph_ok = true;
-    }
-    for (int64_t s = 0; s < n; ++s) OD_BCK(b, cudaGraphLaunch(b->gexec, b->stream));
-    for (od_handle* h : b->runs) h->host_step += n;
-    b->host_step += n;
-    return batch_check(b);
-}
-
-od_handle* od_batch_run(od_batch* b, int32_t r)
-{
-    if (!b || r < 0 || r >= (int)b->runs.size()) return nullptr;
-    return b->runs[r];
-}
-
-int od_batch_size(const od_batch* b) { return b ? (int)b->runs.size() : 0; }
-
-// one tuning launch of the current plan: every run's pair units, then its kick tiles in
-// forces-only mode (fresh counters per configuration)
-static int batch_tune_launch(od_batch* b, int grid)
-{
-    const int lrc = launch_batch(b->ipt, grid, b->d_runs, b->d_tasks_f, b->phase_end_f, b->T_f, b->d_bc_f,
-                                 b->d_done_f, (int)b->runs.size(), SPIN_LIMIT, 1, b->stream);
-    return lrc ? bfail(b, OD_ECUDA, "batch tune launch failed") : OD_OK;
-}
-
-int od_batch_tune(od_batch* b, int reps, double* ms, int* best_ipt, int* best_jc)
-{
-    if (!b || reps < 1) return bfail(b, OD_EINVAL, "bad batch or repetition count");
-    static const int ipts[3] = {1, 2, 4};
-    static const int jcs[4] = {2048, 4096, 8192, 0};  // 0: symmetric tile pairs
-    double best = 1e300;
-    int bi = b->ipt, bj = b->jc;
-    const int R = (int)b->runs.size();
-    for (int a = 0; a < 3; ++a)
-        for (int c = 0; c < 4; ++c) {
-            b->ipt = ipts[a];
-            b->jc = jcs[c];
-            int rc = batch_build(b);
-            if (rc) return rc;
-            OD_BCK(b, cudaMemsetAsync(b->d_bc_f, 0, sizeof(BatchCtrl), b->stream));
-            OD_BCK(b, cudaMemsetAsync(b->d_done_f, 0, sizeof(unsigned long long) * 3 * R, b->stream));
-            const int grid = (int)std::max(1ll, std::min<long long>((long long)batch_blocks_per_sm(b->ipt) * b->sms, b->T_f));
-            if ((rc = batch_tune_launch(b, grid))) return rc;
-            OD_BCK(b, cudaEventRecord(b->e0, b->stream));
-            for (int i = 0; i < reps; ++i)
-                if ((rc = batch_tune_launch(b, grid))) return rc;
-            OD_BCK(b, cudaEventRecord(b->e1, b->stream));
-            OD_BCK(b, cudaEventSynchronize(b->e1));
-            float t = 0.f;
-            OD_BCK(b, cudaEventElapsedTime(&t, b->e0, b->e1));
-            if (ms) ms[a * 4 + c] = t / reps;
-            if (t / reps < best) {
-                best = t / reps;
-                bi = ipts[a];
-                bj = jcs[c];
-            }
-        }
-    b->ipt = bi;
-    b->jc = bj;
-    int rc = batch_build(b);
-    if (rc) return rc;
-    // the accelerations left by the timing belong to other plans: evaluate them again
-    // with the chosen one
-    OD_BCK(b, cudaMemsetAsync(b->d_bc_f, 0, sizeof(BatchCtrl), b->stream));
-    OD_BCK(b, cudaMemsetAsync(b->d_done_f, 0, sizeof(unsigned long long) * 3 * R, b->stream));
-    if ((rc = batch_tune_launch(b, (int)std::max(1ll, std::min<long long>((long long)batch_blocks_per_sm(b->ipt) * b->sms,
-                                                                            b->T_f)))))
-        return rc;
-    if ((rc = batch_check(b))) return rc;
-    if (best_ipt) *best_ipt = bi;
-    if (best_jc) *best_jc = bj;
-    return OD_OK;
-}
-
-int od_batch_set_config(od_batch* b, int ipt, int jc)
-{
-    if (!b || (ipt != 1 && ipt != 2 && ipt != 4) || (jc != 0 && jc < 256))
-        return bfail(b, OD_EINVAL, "bad batch configuration");
-    b->ipt = ipt;
-    b->jc = jc;
-    return batch_build(b);
-}
-
-void od_destroy_batch(od_batch* b)
-{
-    if (!b) return;
-    batch_free(b);
-    delete b;
-}
-
-const char* od_batch_last_error(const od_batch* b) { return b ? b->err.c_str() : g_batch_error.c_str(); }
 
 }  // extern "C"

@@ -1,0 +1,103 @@
+// Host-side internals shared by the translation units of the C ABI: the run handle and
+// the helpers that derive, plan, launch and check its work (od_api.cu), configure its
+// pair kernels (od_config.cu), save and load it (od_io.cu) and step it in batches
+// (od_batch_api.cu).
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "od_internal.h"
+
+struct od_handle {
+    od::Phys P{};
+    od::Bufs B{};
+    od::ForceArgs F{};
+    int variant = 0;
+    int upb = 8;  // pair-kernel work units per persistent block
+    int bps = 0;  // persistent pair-kernel CTAs per SM (0 = occupancy limit)
+    bool batch_member = false;  // stepped only through its batch (od_batch_step)
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    bool graph_ok = false;
+    long long cap = 0;       // ion capacity
+    long long npad_cap = 0;  // fpos capacity
+    long long part_cap = 0;  // partial-sum capacity (float4)
+    long long nb_cap = 0;    // kick blocks capacity
+    long long host_step = 0;
+    long long series_cap = 0;
+    int sms = 0;
+    double alpha[15] = {0};
+    double info[32] = {0};
+    std::string err;
+    bool profiling = false;
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    double kms[4] = {0, 0, 0, 0};
+    long long klaunch[4] = {0, 0, 0, 0};
+    double* d_stats = nullptr;
+    double* d_vtab = nullptr;
+    double* d_series = nullptr;
+    int* d_evseries = nullptr;
+    od_params prm{};                     // creation parameters (pointers cleared): checkpoints
+    od_dust prm_dust[OD_MAX_DUST] = {};
+    unsigned long long* d_hist = nullptr;  // n(r, z) counts [nz][nr] while enabled
+    int hist_nr = 0, hist_nz = 0;
+    long long hist_samples = 0;
+    double* d_io = nullptr;   // device staging of host arrays: x, v, a as [cap][3] each
+    double* h_io = nullptr;   // pinned staging for pageable host arrays (same layout)
+    uint64_t* h_ioid = nullptr;
+    bool cut_on = false;                   // ion-ion cutoff (od_set_cutoff)
+    double r_cut = 0.0, r_switch = 0.0;
+    od::CutBufs C{};
+    int cut_grid = 1;
+};
+
+namespace od {
+namespace host {
+
+// CODATA 2018
+constexpr double kQE = 1.602176634e-19;
+constexpr double kKB = 1.380649e-23;
+constexpr double kEPS0 = 8.8541878128e-12;
+constexpr double kME = 9.1093837015e-31;
+constexpr double kPI = 3.141592653589793238;
+constexpr double kTWO32 = 4294967296.0;
+
+extern thread_local std::string g_create_error;  // od_last_error(NULL)
+
+int fail(od_handle* h, int code, const std::string& msg);
+int cuda_fail(od_handle* h, cudaError_t e, const char* where);
+int validate(const od_params* p, std::string& msg);
+double oml_charge(const od_params* p, double a);
+ForceArgs plan_forces(int N, int v, int sms, int units_per_block, int bps_cap);
+int default_variant(int N);
+int ensure_part(od_handle* h);
+int replan(od_handle* h, int N);
+int launch_pairs(od_handle* h, int after_push);
+int plan_n(const od_handle* h, long long n_live);
+int read_error_word(od_handle* h);
+int force_eval(od_handle* h);
+int ensure_series(od_handle* h, long long need);
+int ensure_io(od_handle* h);
+bool host_pinned(const void* p);
+void free_cut(od_handle* h);
+void free_all(od_handle* h);
+int create_impl(const od_params* p, od_handle* h);
+int apply_force_config(od_handle* h, int variant, int upb, int bps);  // od_config.cu
+
+}  // namespace host
+}  // namespace od
+
+#define OD_CK(h, call)                                      \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
+    } while (0)
+
+#define OD_LK(h, call)                                                       \
+    do {                                                                     \
+        int e_ = (call);                                                     \
+        if (e_ != 0) return cuda_fail(h, (cudaError_t)e_, #call);            \
+    } while (0)
