@@ -318,7 +318,7 @@ __global__ void k_cut_units(const float4* __restrict__ lo, const float4* __restr
 
 // persistent CTAs over the listed tile pairs (their number is read on the device)
 template <int BT, int IPT>
-__global__ void __launch_bounds__(BT) k_forces_cut(const float4* __restrict__ fsort, float4* __restrict__ part,
+__global__ void __launch_bounds__(BT, (IPT == 8 ? 65536 / (BT * 128) : 1)) k_forces_cut(const float4* __restrict__ fsort, float4* __restrict__ part,
                                                    ForceArgs F, const int4* __restrict__ units,
                                                    const int* __restrict__ n_units)
 {
@@ -341,8 +341,8 @@ static int ckc(cudaError_t e) { return e == cudaSuccess ? 0 : (int)e; }
 int cut_blocks_per_sm(int ipt)
 {
     int nb = 0;
-    const void* fn = ipt == 4 ? (const void*)k_forces_cut<256, 4> : (const void*)k_forces_cut<256, 2>;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, 256, 0) != cudaSuccess) return 1;
+    const void* fn = ipt == 4 ? (const void*)k_forces_cut<256, 4> : (const void*)k_forces_cut<64, 8>;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, ipt == 4 ? 256 : 64, 0) != cudaSuccess) return 1;
     return nb > 0 ? nb : 1;
 }
 
@@ -379,8 +379,8 @@ int launch_forces_cut(const Phys& P, const Bufs& B, const ForceArgs& F, const Cu
     k_cut_units<<<wb, 256, 0, s>>>(C.box_lo, C.box_hi, T, C.rs2_tile, C.nbr_start, C.nbr, C.ustart, C.over, C.units);
     if (F.TI == 1024)
         k_forces_cut<256, 4><<<grid, 256, 0, s>>>(C.fsort, B.part, F, C.units, C.n_units);
-    else
-        k_forces_cut<256, 2><<<grid, 256, 0, s>>>(C.fsort, B.part, F, C.units, C.n_units);
+    else  // 512-ion tiles: 64 threads x 8 targets
+        k_forces_cut<64, 8><<<grid, 64, 0, s>>>(C.fsort, B.part, F, C.units, C.n_units);
     return ckc(cudaGetLastError());
 }
 
