@@ -166,8 +166,11 @@ int od_set_ions(od_handle* h, const double* x, const double* v, const double* a,
  * cutoff study); the call re-evaluates the forces of the current state.  At most
  * 2,097,152 ions; OD_EINVAL when the partial sums would need more than 48 GB (a cutoff
  * long against the domain) or on a batch member; od_tune is not available while the
- * cutoff is on.  A step reports OD_EOVERFLOW if the ion density becomes so uneven that
- * a tile's neighbours exceed the slots sized here (calling od_set_cutoff again resizes). */
+ * cutoff is on.  Partial-sum slots per ion: the neighbour tiles of a uniform density with
+ * a margin, grown to the largest neighbour count of the current positions (plus a quarter)
+ * whenever od_set_cutoff, od_set_ions or od_load finds more.  A step whose positions
+ * outgrow them skips its ion-ion forces and reports OD_EOVERFLOW; od_load of an earlier
+ * checkpoint or od_set_ions then resizes the slots and clears the report. */
 int od_set_cutoff(od_handle* h, double r_cut, double r_switch);
 
 /* Checkpoint and restart (the paper's runs last tens of thousands of steps, Sec. 4).

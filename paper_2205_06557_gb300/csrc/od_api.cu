@@ -567,9 +567,40 @@ int read_error_word(od_handle* h)
     if (err & ERR_PLACE) return fail(h, OD_EINVAL, "initial ion placement failed (grains fill the domain?)");
     if (err & ERR_OVERFLOW) return fail(h, OD_EOVERFLOW, "ion capacity exceeded");
     if (err & ERR_CUTCAP)
-        return fail(h, OD_EOVERFLOW, "cutoff: a tile has more neighbour tiles than its partial slots (the ion "
-                                     "density became very uneven); set the cutoff again to resize");
+        return fail(h, OD_EOVERFLOW, "cutoff: a tile had more neighbour tiles than its partial slots (the ion density "
+                                     "became very uneven) and its step ran without ion-ion forces; load a checkpoint "
+                                     "or set the ions again, which resizes the slots");
     return OD_OK;
+}
+
+// The cutoff's slot capacity for the current positions (fpos refreshed): the tile lists
+// are built without evaluating pairs; when a tile has more neighbours than max_deg the
+// capacity grows to the largest degree plus a quarter and eight. The lists are rebuilt at
+// every evaluation, so the overflow bit of an earlier step is cleared here.
+int cut_fit(od_handle* h)
+{
+    if (!h->cut_on) return OD_OK;
+    if (h->P.N > 0 && !(h->P.flags & OD_F_NO_IONION))
+        OD_LK(h, launch_forces_cut(h->P, h->B, h->F, h->C, h->cut_grid, h->stream, 1));
+    int ov[2] = {0, 0}, err = 0;
+    char* const errp = (char*)h->B.ctrl + offsetof(Ctrl, err);
+    if (h->P.N > 0 && !(h->P.flags & OD_F_NO_IONION))
+        OD_CK(h, cudaMemcpyAsync(ov, h->C.over, sizeof(ov), cudaMemcpyDeviceToHost, h->stream));
+    OD_CK(h, cudaMemcpyAsync(&err, errp, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    OD_CK(h, cudaStreamSynchronize(h->stream));
+    err &= ~ERR_CUTCAP;
+    OD_CK(h, cudaMemcpyAsync(errp, &err, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    OD_CK(h, cudaStreamSynchronize(h->stream));  // err is a host local
+    if (!ov[0]) return OD_OK;
+    const long long t_cap = (h->cap + h->F.TI - 1) / h->F.TI;
+    const int md = (int)std::min<long long>(t_cap, (long long)std::ceil(1.25 * ov[1]) + 8);
+    const double slot_bytes = (double)md * (double)(t_cap * h->F.TI) * sizeof(float4);
+    if (slot_bytes > 48e9)
+        return fail(h, OD_EOVERFLOW, "cutoff: the ion density is too uneven for the partial slots (" +
+                                         std::to_string(slot_bytes / 1e9) + " GB)");
+    h->C.max_deg = md;
+    h->graph_ok = false;
+    return replan(h, h->P.N);
 }
 
 // forces for the current state (creation or replaced ions)
@@ -1020,6 +1051,7 @@ int od_set_ions(od_handle* h, const double* x, const double* v, const double* a,
     if ((rc = replan(h, plan_n(h, n)))) return rc;
     h->graph_ok = false;
     OD_LK(h, launch_fpos(h->P, h->B, buf, h->stream));
+    if ((rc = cut_fit(h))) return rc;
     // given accelerations were converted on the device above; otherwise evaluate them
     if (!a && (rc = force_eval(h))) return rc;
     return read_error_word(h);

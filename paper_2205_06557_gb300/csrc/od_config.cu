@@ -110,7 +110,7 @@ int od_set_cutoff(od_handle* h, double r_cut, double r_switch)
     OD_CK(h, cudaMalloc(&C.cnt, sizeof(int) * T));
     OD_CK(h, cudaMalloc(&C.ucnt, sizeof(int) * T));
     OD_CK(h, cudaMalloc(&C.ustart, sizeof(int) * T));
-    OD_CK(h, cudaMalloc(&C.over, sizeof(int)));
+    OD_CK(h, cudaMalloc(&C.over, 2 * sizeof(int)));
     h->cut_on = true;
     h->r_cut = r_cut;
     h->r_switch = r_switch;
@@ -119,6 +119,7 @@ int od_set_cutoff(od_handle* h, double r_cut, double r_switch)
     OD_LK(h, launch_cut_dummies(C, h->P.N, h->F.n_pad, h->stream));
     OD_LK(h, launch_fpos(h->P, h->B, buf, h->stream));
     h->graph_ok = false;
+    if ((rc = cut_fit(h))) return rc;
     if ((rc = force_eval(h))) return rc;
     OD_CK(h, cudaStreamSynchronize(h->stream));
     return read_error_word(h);

@@ -234,20 +234,22 @@ __global__ void __launch_bounds__(1024) k_cut_offsets(const int* __restrict__ cn
                                                       int* __restrict__ over, int* __restrict__ err)
 {
     __shared__ int s_w[32];
-    __shared__ int s_over;
-    if (threadIdx.x == 0) s_over = 0;
+    __shared__ int s_over, s_max;
+    if (threadIdx.x == 0) s_over = s_max = 0;
     __syncthreads();
     constexpr int PER = CUT_MAX_TILES / 1024;
     const int base = threadIdx.x * PER;
-    int v[PER], u[PER], sv = 0, su = 0;
+    int v[PER], u[PER], sv = 0, su = 0, vmax = 0;
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
         v[k] = base + k < T ? cnt[base + k] : 0;
         u[k] = base + k < T ? ucnt[base + k] : 0;
         if (v[k] > max_deg) s_over = 1;
+        vmax = max(vmax, v[k]);
         sv += v[k];
         su += u[k];
     }
+    atomicMax(&s_max, vmax);
     int tv, tu;
     int rv = block_excl_scan(sv, s_w, tv);
     int ru = block_excl_scan(su, s_w, tu);
@@ -263,7 +265,8 @@ __global__ void __launch_bounds__(1024) k_cut_offsets(const int* __restrict__ cn
     if (threadIdx.x == 0) {
         nbr_start[T] = ov ? 0 : tv;
         *n_units = ov ? 0 : tu;
-        *over = ov ? 1 : 0;
+        over[0] = ov ? 1 : 0;
+        over[1] = s_max;
         if (ov) atomicOr(err, ERR_CUTCAP);
     }
 }
@@ -352,7 +355,8 @@ int launch_cut_dummies(const CutBufs& C, int N, int n_pad, cudaStream_t s)
     return ckc(cudaGetLastError());
 }
 
-int launch_forces_cut(const Phys& P, const Bufs& B, const ForceArgs& F, const CutBufs& C, int grid, cudaStream_t s)
+int launch_forces_cut(const Phys& P, const Bufs& B, const ForceArgs& F, const CutBufs& C, int grid, cudaStream_t s,
+                      int lists_only)
 {
     const int N = P.N;
     if (N == 0 || (P.flags & OD_F_NO_IONION)) return 0;
@@ -375,6 +379,7 @@ int launch_forces_cut(const Phys& P, const Bufs& B, const ForceArgs& F, const Cu
     const int wb = (T + 7) / 8;  // 8 warps per CTA, one per tile
     k_cut_count<<<wb, 256, 0, s>>>(C.box_lo, C.box_hi, T, C.rc2_tile, C.cnt, C.ucnt);
     k_cut_offsets<<<1, 1024, 0, s>>>(C.cnt, C.ucnt, T, C.max_deg, C.nbr_start, C.ustart, C.n_units, C.over, C.err);
+    if (lists_only) return ckc(cudaGetLastError());
     k_cut_fill<<<wb, 256, 0, s>>>(C.box_lo, C.box_hi, T, C.rc2_tile, C.nbr_start, C.over, C.nbr);
     k_cut_units<<<wb, 256, 0, s>>>(C.box_lo, C.box_hi, T, C.rs2_tile, C.nbr_start, C.nbr, C.ustart, C.over, C.units);
     if (F.TI == 1024)

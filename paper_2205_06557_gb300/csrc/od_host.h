@@ -79,6 +79,7 @@ int launch_pairs(od_handle* h, int after_push);
 int plan_n(const od_handle* h, long long n_live);
 int read_error_word(od_handle* h);
 int force_eval(od_handle* h);
+int cut_fit(od_handle* h);
 int ensure_series(od_handle* h, long long need);
 int ensure_io(od_handle* h);
 bool host_pinned(const void* p);

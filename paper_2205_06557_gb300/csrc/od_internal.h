@@ -202,11 +202,13 @@ struct CutBufs {
     int* cnt;        // [T] neighbours per tile
     int* ucnt;       // [T] tile pairs (J >= I) per tile
     int* ustart;     // [T] first unit of each tile
-    int* over;       // 1: the lists exceed max_deg
+    int* over;       // [0] 1: the lists exceed max_deg; [1] largest tile degree of the last lists
     int max_deg;     // slot capacity per ion
     int* err;        // the run's error word (Ctrl::err)
 };
-int launch_forces_cut(const Phys& P, const Bufs& B, const ForceArgs& F, const CutBufs& C, int grid, cudaStream_t s);
+// lists_only: sort, boxes, degrees and the overflow check, no pair evaluation
+int launch_forces_cut(const Phys& P, const Bufs& B, const ForceArgs& F, const CutBufs& C, int grid, cudaStream_t s,
+                      int lists_only = 0);
 int launch_cut_dummies(const CutBufs& C, int N, int n_pad, cudaStream_t s);
 int cut_blocks_per_sm(int ipt);
 

@@ -260,6 +260,8 @@ int od_load(const char* path, void* cuda_stream, od_handle** out)
         if ((rc = replan(h, plan_n(h, N)))) return done(rc);
         if (launch_fpos(h->P, h->B, buf, h->stream)) return done(fail(h, OD_ECUDA, "position refresh failed"));
     }
+    // slot capacity for the saved positions (the saved accelerations stay)
+    if ((rc = cut_fit(h))) return done(rc);
     h->graph_ok = false;
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return done(fail(h, OD_ECUDA, "checkpoint upload failed"));
     return done(read_error_word(h));

@@ -135,6 +135,48 @@ def test_cutoff_is_deterministic_and_checkpoints_exactly(tmp_path):
     c.step(2)
 
 
+def test_uneven_density_grows_the_partial_slots(tmp_path):
+    """All 16,384 ions of a 12 mm tube gathered within |z| < r_cut / 2: each of the 32 tiles
+    then neighbours all 32, beyond the 21 slots sized for the uniform density. Setting the
+    ions measures the degrees and grows the slots (the lists overflowed, and the call
+    failed with OD_EOVERFLOW, before); the forces match the oracle; the cutoff set on the
+    gathered state gives the same bits; a checkpoint of it loads and continues exactly."""
+    n = 16384
+    p = _tube(H=1.2e-2, n_ions=n, r_cut=RC, r_switch=RS)
+    p["alpha"] = oracle.Oracle(dict(p, n_ions=1)).alpha()
+    x, v, ids = W.random_ions(n, p["R"], RC, seed=4242, dust=p["dust"])
+    run = od.Run(p)
+    od.od_set_cutoff(run.h, RC, RS)
+    run.set_ions(x, v, ids, next_id=n)
+    o = oracle.Oracle(p)
+    o.set_ions(x, v, ids)
+    acc_ref, fo_ref = o.forces()
+    _, _, a_gpu, _ = run.get_ions()
+    d = o.derived()
+    kii = d["q"] ** 2 / (4 * math.pi * EPS0 * d["m"])
+    psum, pbound = _scales(x, d["lam"], kii, RC)
+    dev = np.linalg.norm(a_gpu - acc_ref, axis=1)
+    assert np.linalg.norm(a_gpu - acc_ref) <= 1e-5 * np.linalg.norm(acc_ref)
+    err = (dev - 2 * pbound) / (psum + np.linalg.norm(acc_ref, axis=1))
+    assert err.max() < 1e-5, (err.max(), int(err.argmax()))
+    _, fo_gpu = run.dust_now()
+    assert np.allclose(fo_gpu, fo_ref, rtol=1e-5, atol=1e-5 * np.abs(fo_ref).max())
+    late = od.Run(p)
+    late.set_ions(x, v, ids, next_id=n)
+    od.od_set_cutoff(late.h, RC, RS)
+    assert np.array_equal(late.get_ions()[2], a_gpu)
+    late.close()
+    path = str(tmp_path / "gathered.ckpt")
+    run.save(path)
+    back = od.Run.load(path)
+    run.step(3)
+    back.step(3)
+    for got, want in zip(back.get_ions(), run.get_ions()):
+        assert np.array_equal(got, want)
+    run.close()
+    back.close()
+
+
 def test_bad_cutoffs_are_rejected():
     run = od.Run(W.tiny())
     for rc, rs in [(1e-4, 2e-4), (1e-4, -1e-5), (float("nan"), 0.0)]:
