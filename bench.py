@@ -62,7 +62,7 @@ def parse():
     ap.add_argument("--eval-steps", type=int, default=100000)
     ap.add_argument("--runs", type=int, default=64)
     ap.add_argument("--e2e-steps", type=int, default=5)
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--pair-config", default="tuned",
                     help="pair-kernel choice 'variant,units_per_block,ctas_per_sm' instead of the autotuner's")
@@ -149,8 +149,9 @@ def cpu_baseline(p, seconds):
     n = int(round(p["n_inf"] * math.pi * p["R"] ** 2 * p["H"] / p.get("weight", 1.0)))
     x, v, ids = W.random_ions(n, p["R"], p["H"], seed=12345, dust=p["dust"])
     o.load_ions(x, v, ids)
+    # calibrate on 64 targets per thread (fewer leave the threads' start-up dominant)
     t0 = time.perf_counter()
-    m0 = min(64, n)
+    m0 = min(64 * oracle.num_threads(), n)
     o.forces(0, m0, dust=False)
     rate = m0 / max(time.perf_counter() - t0, 1e-6)
     m = int(max(m0, min(n, rate * seconds)))
@@ -173,8 +174,9 @@ def run_reference(args):
     x, v, ids = W.random_ions(n, p["R"], p["H"], seed=12345, dust=p["dust"])
     o.load_ions(x, v, ids)
     t0 = time.perf_counter()
-    o.forces(0, 64, dust=False)
-    rate = 64 / (time.perf_counter() - t0)
+    m0 = min(64 * oracle.num_threads(), n)
+    o.forces(0, m0, dust=False)
+    rate = m0 / max(time.perf_counter() - t0, 1e-6)
     m = int(max(64, min(n, rate * 120.0 / max(args.steps + args.warmup, 1))))
     for s in range(args.warmup):
         o.forces((s * m) % n, min(n, (s * m) % n + m), dust=False)

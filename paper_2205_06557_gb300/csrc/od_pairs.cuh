@@ -308,8 +308,25 @@ __device__ __forceinline__ f32x2 pair_c3x2(f32x2 dx, f32x2 dy, f32x2 dz)
     return mul2(mul2(e, mul2(ri, ri)), add2(ri, ln2));
 }
 
+// switch_bracket for two pairs at once, in packed operations (only the clamp is per
+// lane): x = (s - s0) w_inv in [0, 1], S = 1 + x^3 (15 x - 6 x^2 - 10),
+// -S' = 30 x^2 (1 - x)^2, bracket = (ri + ln2) S + 30 w_inv x^2 (1 - x)^2
+__device__ __forceinline__ f32x2 switch_bracket2(f32x2 s, f32x2 ri, float s0, float w_inv)
+{
+    constexpr float LN2 = 0.69314718055994531f;
+    f32x2 x = fma2(s, pk2(w_inv, w_inv), pk2(-s0 * w_inv, -s0 * w_inv));
+    float xa, xb;
+    upk2(x, xa, xb);
+    x = pk2(fminf(fmaxf(xa, 0.f), 1.f), fminf(fmaxf(xb, 0.f), 1.f));
+    const f32x2 x2 = mul2(x, x);
+    const f32x2 t = fma2(fma2(x, pk2(-6.f, -6.f), pk2(15.f, 15.f)), x, pk2(-10.f, -10.f));
+    const f32x2 S = fma2(mul2(x2, x), t, pk2(1.f, 1.f));
+    const f32x2 y2 = fma2(x, add2(x, pk2(-2.f, -2.f)), pk2(1.f, 1.f));
+    return fma2(mul2(x2, y2), pk2(30.f * w_inv, 30.f * w_inv), mul2(add2(ri, pk2(LN2, LN2)), S));
+}
+
 // pair_c3_cut for two pairs at once: the packed plain coefficient's steps, then the
-// switching bracket per lane
+// packed switching bracket
 __device__ __forceinline__ f32x2 pair_c3x2_cut(f32x2 dx, f32x2 dy, f32x2 dz, float s0, float w_inv)
 {
     const f32x2 eps2 = pk2(1e-24f, 1e-24f);
@@ -318,13 +335,12 @@ __device__ __forceinline__ f32x2 pair_c3x2_cut(f32x2 dx, f32x2 dy, f32x2 dz, flo
     r2 = fma2(dz, dz, r2);
     float ra, rb;
     upk2(r2, ra, rb);
-    const float ria = rsqrt_approx(ra), rib = rsqrt_approx(rb);
-    const f32x2 ri = pk2(ria, rib);
+    const f32x2 ri = pk2(rsqrt_approx(ra), rsqrt_approx(rb));
+    const f32x2 s = mul2(r2, ri);
     float sa, sb;
-    upk2(mul2(r2, ri), sa, sb);
+    upk2(s, sa, sb);
     const f32x2 e = pk2(ex2_approx(-sa), ex2_approx(-sb));
-    const f32x2 br = pk2(switch_bracket(sa, ria, s0, w_inv), switch_bracket(sb, rib, s0, w_inv));
-    return mul2(mul2(e, mul2(ri, ri)), br);
+    return mul2(mul2(e, mul2(ri, ri)), switch_bracket2(s, ri, s0, w_inv));
 }
 
 constexpr int SYM_SUB = 128;  // sources per combine step of the symmetric kernels
