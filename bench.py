@@ -31,12 +31,15 @@ from paper_2205_06557_gb300 import workloads as W  # noqa: E402
 
 METRIC = "ion pair-interactions/s"
 UNIT = "pairs/s"
-# ALU roofline of the pair kernels, in ordered pairs per clock per SM: min(128 FP32 lanes /
-# FP32 ops per ordered pair, 16 MUFU lanes / MUFU ops per ordered pair).  The ordered-pair
-# kernel spends 14 FP32 ops and 2 MUFU (rsqrt, ex2) on each ordered pair; the symmetric one
-# 17 FP32 ops (3 more for the source's sum) and 2 MUFU on each unordered pair, applied to
-# both ions, i.e. 8.5 FP32 and 1 MUFU per ordered pair.
-PAIRS_PER_CLK_SM = {0: min(128 / 14, 16 / 2), 1: min(128 / 8.5, 16 / 1), 2: min(128 / 8.5, 16 / 1)}
+# ALU roofline of the pair kernels, in ordered pairs per clock per SM: the FP32 pipe (128
+# lanes) and the SFU, whose MUFU rsqrt runs at 16 and MUFU ex2 at 32 lanes per clock per SM on
+# GB300 (od_measure_peaks).  The ordered-pair kernel spends 14 FP32 ops, one rsqrt and one
+# ex2 on each ordered pair; the symmetric one 17 FP32 ops (3 more for the source's sum), one
+# rsqrt and one ex2 on each unordered pair, applied to both ions, i.e. 8.5 FP32 ops and half
+# of each MUFU per ordered pair.  Both are FP32-pipe bound.
+SFU_CLK_PER_PAIR = 1 / 16 + 1 / 32
+PAIRS_PER_CLK_SM = {0: min(128 / 14, 1 / SFU_CLK_PER_PAIR), 1: min(128 / 8.5, 2 / SFU_CLK_PER_PAIR),
+                    2: min(128 / 8.5, 2 / SFU_CLK_PER_PAIR)}
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch, from the full ncu capture of
 # that kernel on that ion count (profiles/k_forces_at_scale_200k.md and
 # profiles/k_forces_sym_at_scale_200k.md); any other kernel or size reports null until it
@@ -304,7 +307,7 @@ def run_ours(args):
                      "unit": "Gpair/s", "frac": k1_rate / peak, "traffic": NCU_DRAM_BYTES.get((kname, N)),
                      "peak_basis": "%d SMs x %.0f MHz x %.2f ordered pairs/clk/SM (FP32 pipe and SFU limits of %s)"
                                    % (sms, clk_max, PAIRS_PER_CLK_SM[sym],
-                                      "17 FP32 + 2 MUFU per unordered pair" if sym else "14 FP32 + 2 MUFU per pair")},
+                                      "17 FP32 + rsqrt + ex2 per unordered pair" if sym else "14 FP32 + rsqrt + ex2 per pair")},
         "clocks": clk,
         "gpu_launches": 4 * args.steps * world,
         "e2e": {"value": e2e_units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

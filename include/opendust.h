@@ -245,11 +245,12 @@ int od_tune(od_handle* h, int reps, double* ms, int* best_variant, int* best_uni
 int od_set_force_config(od_handle* h, int variant, int units_per_block, int blocks_per_sm);
 int od_get_force_config(od_handle* h, int* variant, int* units_per_block, int* blocks_per_sm, int* n_variants);
 
-/* Pipe micro-benchmarks of the current GPU (the ALU roofline of the pair kernel): out[7] =
- * FP32 FMA / clk / SM, MUFU rsqrt / clk / SM, MUFU ex2 / clk / SM, FP64 FMA / clk / SM,
- * dependent FP64 FMA latency (clk), dependent FP64 exp latency (clk), the SM clock (MHz)
- * the per-clock rates are normalised by.  Rates use the nominal clock: rescale by the
- * clock measured while they ran. */
+/* Pipe micro-benchmarks of the current GPU (the ALU roofline of the pair kernel), host
+ * double[9]: operations per second per SM of FP32 FMA, MUFU rsqrt, MUFU ex2 and FP64 FMA;
+ * the latency (ns) of a dependent FP64 FMA and of a dependent FP64 exp; the device's
+ * maximum SM clock (MHz); operations per second per SM of MUFU rcp and MUFU lg2.  Divide
+ * by the SM clock seen while they ran for per-clock rates.  Each rate comes from 64 warps
+ * per SM with eight independent chains each (throughput, not latency); about 10 ms in all. */
 int od_measure_peaks(double* out);
 
 /* OML floating charge (C) of an isolated grain of the given radius in the plasma and flow

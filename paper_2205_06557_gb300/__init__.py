@@ -130,6 +130,8 @@ def lib():
             getattr(L, name).restype = ctypes.c_int
         L.od_oml_charge.argtypes = [P(od_params), ctypes.c_double, vp]
         L.od_oml_charge.restype = ctypes.c_int
+        L.od_measure_peaks.argtypes = [vp]
+        L.od_measure_peaks.restype = ctypes.c_int
         L.od_sur_create.argtypes = [ctypes.c_int, ctypes.c_uint64, vp, P(vp)]
         L.od_sur_destroy.argtypes = [vp]
         L.od_sur_destroy.restype = None
@@ -203,6 +205,18 @@ def od_oml_charge(p, radius):
     q = ctypes.c_double()
     _check(lib().od_oml_charge(ctypes.byref(s), float(radius), ctypes.byref(q)))
     return q.value
+
+
+def od_measure_peaks(clock_mhz=None):
+    """Pipe rates of the current GPU (od_measure_peaks): operations per second per SM of
+    FP32 FMA, MUFU rsqrt / ex2 / rcp / lg2 and FP64 FMA, and the same per SM clock, using
+    clock_mhz (the clock seen while they ran) or else the device's maximum clock."""
+    out = np.zeros(9)
+    _check(lib().od_measure_peaks(out.ctypes.data_as(ctypes.c_void_p)))
+    mhz = float(clock_mhz or out[6])
+    per_s = {"ffma": out[0], "rsqrt": out[1], "ex2": out[2], "rcp": out[7], "lg2": out[8], "dfma": out[3]}
+    return {"per_s_per_sm": per_s, "per_clk_per_sm": {k: v / (mhz * 1e6) for k, v in per_s.items()},
+            "clock_mhz": mhz, "max_clock_mhz": out[6], "dfma_latency_ns": out[4], "dexp_latency_ns": out[5]}
 
 
 def od_create(p, stream=None):

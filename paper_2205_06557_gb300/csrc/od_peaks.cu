@@ -28,22 +28,26 @@ __global__ void k_ffma(float* out, int iters, float a, float b)
     if (s == 12345.678f) out[0] = s;
 }
 
+// one MUFU function per chain step: rsqrt (0), ex2 of the negated value (1, the negation is
+// an operand modifier), rcp (2) and lg2 (3) of the value plus a constant (one FADD)
 __global__ void k_mufu(float* out, int iters, int which)
 {
     float x[CHAINS];
 #pragma unroll
-    for (int c = 0; c < CHAINS; ++c) x[c] = 1.0f + threadIdx.x * 1e-7f + c * 1e-3f;
+    for (int c = 0; c < CHAINS; ++c) x[c] = 0.5f + threadIdx.x * 1e-7f + c * 1e-3f;
     for (int i = 0; i < iters; ++i)
 #pragma unroll
         for (int c = 0; c < CHAINS; ++c) {
             float r;
-            if (which == 0) {
-                asm volatile("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x[c]));
-                x[c] = r;  // converges to 1
-            } else {
-                asm volatile("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x[c]));
-                x[c] = r - 1.5f;  // stays bounded (fixed point near -1)
-            }
+            if (which == 0)
+                asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x[c]));  // converges to 1
+            else if (which == 1)
+                asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(-x[c]));  // stays in (0.5, 1)
+            else if (which == 2)
+                asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x[c] + 1.0f));  // stays in (0.5, 1)
+            else
+                asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x[c] + 2.0f));  // stays in (1, 2)
+            x[c] = r;
         }
     float s = 0.f;
 #pragma unroll
@@ -80,8 +84,9 @@ using namespace od::peaks;
 
 extern "C" int od_measure_peaks(double* out)
 {
-    // out: [0] FFMA/clk/SM  [1] rsqrt/clk/SM  [2] ex2/clk/SM  [3] DFMA/clk/SM
-    //      [4] dependent DFMA latency (clk)  [5] dependent FP64 exp latency (clk)  [6] SM clock MHz (events)
+    // out: [0] FFMA  [1] rsqrt  [2] ex2  [3] DFMA  (operations per second per SM)
+    //      [4] dependent DFMA latency (ns)  [5] dependent FP64 exp latency (ns)
+    //      [6] the device's maximum SM clock (MHz)  [7] rcp  [8] lg2 (operations per second per SM)
     if (!out) return OD_EINVAL;
     int dev = 0, sms = 0, clk_khz = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return OD_ENODEV;
@@ -93,6 +98,7 @@ extern "C" int od_measure_peaks(double* out)
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
+    // 8 CTAs of 256 per SM: 64 warps with 8 independent chains each keep every pipe full
     const int blocks = sms * 8, threads = 256;
     auto time_ms = [&](auto launch) {
         launch();
@@ -104,25 +110,24 @@ extern "C" int od_measure_peaks(double* out)
         cudaEventElapsedTime(&ms, e0, e1);
         return (double)ms;
     };
-    // clock-normalised rates use a dependent-FMA chain timing as the clock estimate
-    const int it = 4096;
-    const double total_threads = (double)blocks * threads;
-    const double t_ffma = time_ms([&] { k_ffma<<<blocks, threads>>>(fbuf, it, 1.0000001f, 1e-7f); });
-    const double t_rsq = time_ms([&] { k_mufu<<<blocks, threads>>>(fbuf, it, 0); });
-    const double t_ex2 = time_ms([&] { k_mufu<<<blocks, threads>>>(fbuf, it, 1); });
+    const int it = 4096, it_f = 4 * it;
+    const double per_sm = (double)blocks * threads * CHAINS / sms;
+    const double t_ffma = time_ms([&] { k_ffma<<<blocks, threads>>>(fbuf, it_f, 1.0000001f, 1e-7f); });
+    double t_mufu[4];
+    for (int w = 0; w < 4; ++w) t_mufu[w] = time_ms([&] { k_mufu<<<blocks, threads>>>(fbuf, it, w); });
     const double t_dfma = time_ms([&] { k_dfma<<<blocks, threads>>>(dbuf, it / 16, 0.9999999, 1e-7); });
     const int lit = 20000;
     const double t_dlat = time_ms([&] { k_dlat<<<1, 1>>>(dbuf, lit, 0); });
     const double t_dexp = time_ms([&] { k_dlat<<<1, 1>>>(dbuf, lit / 10, 1); });
-    const double f_hz = clk_khz * 1e3;  // nominal; the caller rescales with the measured clock
-    const double ops_f = total_threads * it * CHAINS;
-    out[0] = ops_f / (t_ffma * 1e-3) / f_hz / sms;
-    out[1] = ops_f / (t_rsq * 1e-3) / f_hz / sms;
-    out[2] = ops_f / (t_ex2 * 1e-3) / f_hz / sms;
-    out[3] = total_threads * (it / 16) * CHAINS / (t_dfma * 1e-3) / f_hz / sms;
-    out[4] = t_dlat * 1e-3 * f_hz / lit;
-    out[5] = t_dexp * 1e-3 * f_hz / (lit / 10);
+    out[0] = per_sm * it_f / (t_ffma * 1e-3);
+    out[1] = per_sm * it / (t_mufu[0] * 1e-3);
+    out[2] = per_sm * it / (t_mufu[1] * 1e-3);
+    out[3] = per_sm * (it / 16) / (t_dfma * 1e-3);
+    out[4] = t_dlat * 1e6 / lit;
+    out[5] = t_dexp * 1e6 / (lit / 10);
     out[6] = clk_khz * 1e-3;
+    out[7] = per_sm * it / (t_mufu[2] * 1e-3);
+    out[8] = per_sm * it / (t_mufu[3] * 1e-3);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(fbuf);
