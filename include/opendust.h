@@ -270,14 +270,15 @@ int od_oml_charge(const od_params* p, double radius, double* Q);
  *                     od_counters, od_get_ions, od_info ...); the batch owns it: do not
  *                     destroy it, step it, replace its ions or tune it on its own
  *   od_batch_tune     times every run's pair tasks followed by its kick tiles (accelerations
- *                     only) at targets-per-thread {1,2,4} x source chunk {2048, 4096, 8192,
- *                     0}, where chunk 0 means symmetric tile pairs of 256 x targets-per-
+ *                     only) at targets-per-thread {2,4,8} x source chunk {2048, 4096, 8192,
+ *                     0}, where chunk 0 means symmetric tile pairs of 128 x targets-per-
  *                     thread ions (each unordered pair once, packed FP32 pairs, one partial
  *                     slot per tile for every ion); ms[12] (host, may be NULL) gets the
  *                     average ms per launch, [ipt index][chunk index]; keeps the fastest and
  *                     recomputes the accelerations with it; positions, velocities and
  *                     grain state are not changed
- *   od_batch_set_config applies a known choice (chunk 0 or >= 256); od_destroy_batch
+ *   od_batch_set_config applies a known choice (targets per thread 2, 4 or 8; chunk 0
+ *                     or >= 256); od_destroy_batch
  *                     frees everything
  *   od_batch_last_error text of the last error on b (or of the last failed create). */
 typedef struct od_batch od_batch;

@@ -464,7 +464,7 @@ def od_batch_run(b, r):
     return ctypes.c_void_p(lib().od_batch_run(b, int(r)))
 
 
-BATCH_TPT = (1, 2, 4)
+BATCH_TPT = (2, 4, 8)
 BATCH_CHUNKS = (2048, 4096, 8192, 0)  # 0: symmetric tile pairs
 
 

@@ -777,7 +777,10 @@ int create_impl(const od_params* p, od_handle* h)
     }
     OD_CK(h, cudaMalloc(&B.acc, sizeof(float4) * h->npad_cap));
     OD_CK(h, cudaMalloc(&B.fpos, sizeof(float4) * h->npad_cap));
-    const long long ntiles = (h->cap + push_tile() - 1) / push_tile();
+    // one status word per scan tile: single runs scan 256-ion tiles, batch members 128
+    const long long scan_tile = std::min(push_tile(), BATCH_TILE);
+    const long long ntiles = (h->cap + scan_tile - 1) / scan_tile;
+    h->scan_tiles_cap = ntiles;
     OD_CK(h, cudaMalloc(&B.tile_status, sizeof(unsigned long long) * ntiles));
     OD_CK(h, cudaMemsetAsync(B.tile_status, 0, sizeof(unsigned long long) * ntiles, h->stream));
     OD_CK(h, cudaMalloc(&B.inj, sizeof(Inj) * h->cap));

@@ -1,7 +1,7 @@
 // Batched persistent step: many independent runs of uneven ion count advance one
 // step in ONE kernel launch (replayed from a CUDA graph).
 //
-// Every run's step is split into tasks of its four phases (scan tiles of 256 ions,
+// Every run's step is split into tasks of its four phases (scan tiles of 128 ions,
 // pair units of one target tile x one source chunk, kick tiles, one grain-tail task).
 // A persistent grid of at most the resident number of CTAs takes tasks from a global
 // counter in phase-major order (all scan tiles, then all pair units, then all kick
@@ -35,8 +35,9 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64c(const unsigned lon
 // tiles wait for their run's pair units as in a step (on the tuning launch's own counters)
 // and evaluate accelerations only (kick mode 1: no velocity update, no collisions), so the
 // runs' states are not changed.
+// held to 128 registers: four CTAs of 128 per SM
 template <int IPT>
-__global__ void __launch_bounds__(BATCH_BT, 2)
+__global__ void __launch_bounds__(BATCH_BT, 65536 / (BATCH_BT * 128))
     k_batch_step(const RunDesc* __restrict__ runs, const int2* __restrict__ tasks, int4 phase_end, long long T,
                  BatchCtrl* bc, unsigned long long* done, int R, long long spin_limit, int tune)
 {
@@ -110,9 +111,9 @@ __global__ void __launch_bounds__(BATCH_BT, 2)
 static void* batch_fn(int ipt)
 {
     switch (ipt) {
-    case 1: return (void*)k_batch_step<1>;
     case 2: return (void*)k_batch_step<2>;
-    default: return (void*)k_batch_step<4>;
+    case 4: return (void*)k_batch_step<4>;
+    default: return (void*)k_batch_step<8>;
     }
 }
 
@@ -127,14 +128,14 @@ int launch_batch(int ipt, int grid, const RunDesc* runs, const int2* tasks, int4
                  BatchCtrl* bc, unsigned long long* done, int R, long long spin_limit, int tune, cudaStream_t s)
 {
     switch (ipt) {
-    case 1:
-        k_batch_step<1><<<grid, BATCH_BT, 0, s>>>(runs, tasks, phase_end, T, bc, done, R, spin_limit, tune);
-        break;
     case 2:
         k_batch_step<2><<<grid, BATCH_BT, 0, s>>>(runs, tasks, phase_end, T, bc, done, R, spin_limit, tune);
         break;
-    default:
+    case 4:
         k_batch_step<4><<<grid, BATCH_BT, 0, s>>>(runs, tasks, phase_end, T, bc, done, R, spin_limit, tune);
+        break;
+    default:
+        k_batch_step<8><<<grid, BATCH_BT, 0, s>>>(runs, tasks, phase_end, T, bc, done, R, spin_limit, tune);
         break;
     }
     const cudaError_t e = cudaGetLastError();

@@ -75,6 +75,8 @@ int batch_build(od_batch* b)
         desc[r].F = h->F;
         desc[r].nA = (h->P.N + BATCH_TILE - 1) / BATCH_TILE;
         desc[r].nK = desc[r].nA;
+        if (desc[r].nA > h->scan_tiles_cap || desc[r].nK > h->nb_cap)
+            return bfail(b, OD_EINVAL, "batch: run " + std::to_string(r) + " has more scan or kick tiles than its buffers");
         for (int i = 0; i < desc[r].nA; ++i) tA.push_back(make_int2(r, i));
         for (long long u = 0; u < h->F.U; ++u) tF.push_back(make_int2(r, (int)u));
         for (int i = 0; i < desc[r].nK; ++i) tK.push_back(make_int2(r, i));
@@ -263,7 +265,7 @@ static int batch_tune_launch(od_batch* b, int grid)
 int od_batch_tune(od_batch* b, int reps, double* ms, int* best_ipt, int* best_jc)
 {
     if (!b || reps < 1) return bfail(b, OD_EINVAL, "bad batch or repetition count");
-    static const int ipts[3] = {1, 2, 4};
+    static const int ipts[3] = {2, 4, 8};
     static const int jcs[4] = {2048, 4096, 8192, 0};  // 0: symmetric tile pairs
     double best = 1e300;
     int bi = b->ipt, bj = b->jc;
@@ -311,7 +313,7 @@ int od_batch_tune(od_batch* b, int reps, double* ms, int* best_ipt, int* best_jc
 
 int od_batch_set_config(od_batch* b, int ipt, int jc)
 {
-    if (!b || (ipt != 1 && ipt != 2 && ipt != 4) || (jc != 0 && jc < 256))
+    if (!b || (ipt != 2 && ipt != 4 && ipt != 8) || (jc != 0 && jc < 256))
         return bfail(b, OD_EINVAL, "bad batch configuration");
     b->ipt = ipt;
     b->jc = jc;

@@ -652,9 +652,10 @@ __device__ __forceinline__ void dust_body(const Phys& P, const Bufs& B, int nb, 
     __shared__ double s_rec[MAXD][REC];
     Ctrl* C = B.ctrl;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // deterministic reduction of the kick kernel's per-block grain sums: warp w takes
-    // component pairs w, w+8, ...; lanes stride the blocks, then a fixed shuffle tree
-    for (int pc = warp; pc < P.D * 3; pc += DUST_BT / 32) {
+    // deterministic reduction of the kick kernel's per-block grain sums: warp w of the nw
+    // in the CTA (8 alone, 4 inside a batch) takes components w, w + nw, ...; lanes
+    // stride the blocks, then a fixed shuffle tree (the same order for any nw)
+    for (int pc = warp; pc < P.D * 3; pc += (int)(blockDim.x >> 5)) {
         const int k = pc / 3, c = pc % 3;
         double s = 0.0;
         for (int b = lane; b < nb; b += 32) s += B.dpart[((long long)b * MAXD + k) * 3 + c];

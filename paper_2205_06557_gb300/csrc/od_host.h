@@ -26,6 +26,7 @@ struct od_handle {
     long long npad_cap = 0;  // fpos capacity
     long long part_cap = 0;  // partial-sum capacity (float4)
     long long nb_cap = 0;    // kick blocks capacity
+    long long scan_tiles_cap = 0;  // scan tile status words (tiles of the smaller of the single-run and batch scan)
     long long host_step = 0;
     long long series_cap = 0;
     int sms = 0;

@@ -156,7 +156,7 @@ struct BatchCtrl {
     int err;
 };
 
-constexpr int BATCH_TILE = 256;  // ions per scan / kick tile and threads per CTA of a batch
+constexpr int BATCH_TILE = 128;  // ions per scan / kick tile and threads per CTA of a batch
 ForceArgs batch_plan(int N, int ipt, int jc);
 int batch_blocks_per_sm(int ipt);
 int launch_batch(int ipt, int grid, const RunDesc* runs, const int2* tasks, int4 phase_end, long long T,

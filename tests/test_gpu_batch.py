@@ -66,7 +66,7 @@ def test_batch_tuning_keeps_results():
     ps = _params()[:2]
     batch = od.Batch(ps)
     ms, ipt, jc = batch.tune(reps=1)
-    assert ms.shape == (3, 4) and ms.min() > 0 and ipt in (1, 2, 4) and jc in (2048, 4096, 8192, 0)
+    assert ms.shape == (3, 4) and ms.min() > 0 and ipt in od.BATCH_TPT and jc in od.BATCH_CHUNKS
     assert ms[od.BATCH_TPT.index(ipt), od.BATCH_CHUNKS.index(jc)] == ms.min()
     singles = [od.Run(p) for p in ps]
     batch.step(15)
@@ -77,7 +77,7 @@ def test_batch_tuning_keeps_results():
     batch.close()
 
 
-@pytest.mark.parametrize("tpt", [1, 2, 4])
+@pytest.mark.parametrize("tpt", od.BATCH_TPT)
 def test_batch_symmetric_plan_reproduces_single_runs(tpt):
     """the batch's symmetric tile pairs (each unordered pair once) give the same events
     and trajectories as the runs stepped alone"""
