@@ -537,6 +537,7 @@ int replan(od_handle* h, int N)
     } else {
         h->F = h->cut_on ? plan_cut(h, N) : plan_forces(N, h->variant, h->sms, h->upb, h->bps);
     }
+    h->F.sched = h->d_sched;
     h->P.n_pad = h->F.n_pad;
     if (h->F.n_pad > h->npad_cap) return fail(h, OD_EOVERFLOW, "padded ion count exceeds the buffer");
     return ensure_part(h);
@@ -710,6 +711,7 @@ void free_all(od_handle* h)
     cudaFree(h->B.dpart);
     cudaFree(h->B.ctrl);
     cudaFree(h->d_stats);
+    cudaFree(h->d_sched);
     cudaFree(h->d_vtab);
     cudaFree(h->d_series);
     cudaFree(h->d_evseries);
@@ -788,6 +790,8 @@ int create_impl(const od_params* p, od_handle* h)
     OD_CK(h, cudaMalloc(&B.dpart, sizeof(double) * h->nb_cap * MAXD * 3));
     OD_CK(h, cudaMalloc(&B.ctrl, sizeof(Ctrl)));
     OD_CK(h, cudaMalloc(&h->d_stats, sizeof(double) * 2 * MAXD * REC));
+    OD_CK(h, cudaMalloc(&h->d_sched, 2 * sizeof(unsigned long long)));
+    OD_CK(h, cudaMemsetAsync(h->d_sched, 0, 2 * sizeof(unsigned long long), h->stream));
     Ctrl c0;
     std::memset(&c0, 0, sizeof(c0));
     c0.next_id = (unsigned long long)N;

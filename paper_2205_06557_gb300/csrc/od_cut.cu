@@ -327,16 +327,18 @@ __global__ void __launch_bounds__(BT, (IPT == 8 ? 65536 / (BT * 128) : 1)) k_for
 {
     __shared__ float s_acc[2][3][BT / 32][SYM_SUB];
     __shared__ float4 sj[BT];
+    __shared__ long long s_u;
     const long long U = *n_units;
-    long long u = (long long)blockIdx.x * U / gridDim.x;
-    const long long u_end = (long long)(blockIdx.x + 1) * U / gridDim.x;
-    for (; u < u_end; ++u) {
+    for (;;) {
+        const long long u = next_unit(F.sched, s_u);
+        if (u >= U) break;
         const int4 t = units[u];  // (I, J, slot of J in I's list, slot of I in J's list | flag)
         if (t.w & CUT_PLAIN)
             sym2_unit<BT, IPT, false>(fsort, part, F, t.x, t.y, s_acc, sj, t.z, t.w & (CUT_PLAIN - 1));
         else
             sym2_unit<BT, IPT, true>(fsort, part, F, t.x, t.y, s_acc, sj, t.z, t.w);
     }
+    leave_queue(F.sched);
 }
 
 static int ckc(cudaError_t e) { return e == cudaSuccess ? 0 : (int)e; }
@@ -360,6 +362,7 @@ int launch_forces_cut(const Phys& P, const Bufs& B, const ForceArgs& F, const Cu
 {
     const int N = P.N;
     if (N == 0 || (P.flags & OD_F_NO_IONION)) return 0;
+    if (!F.sched) return (int)cudaErrorInvalidValue;
     const int nblk = (N + 31) / 32;
     const long long M = (long long)C.nslab * nblk;
     int rc;

@@ -38,6 +38,7 @@ struct od_handle {
     double kms[4] = {0, 0, 0, 0};
     long long klaunch[4] = {0, 0, 0, 0};
     double* d_stats = nullptr;
+    unsigned long long* d_sched = nullptr;  // unit queue of the symmetric and cutoff pair kernels
     double* d_vtab = nullptr;
     double* d_series = nullptr;
     int* d_evseries = nullptr;

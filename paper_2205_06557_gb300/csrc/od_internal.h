@@ -137,6 +137,9 @@ struct ForceArgs {
     float cut_s0, cut_inv_w;
     const int* nbr_start;
     const int* rank;
+    // dynamic unit queue of the packed symmetric and cutoff kernels: [0] next unit,
+    // [1] CTAs finished (both zero between launches)
+    unsigned long long* sched;
 };
 
 // One run of a batched launch (od_batch.cu): its parameters, buffers and pair plan.
@@ -144,8 +147,8 @@ struct RunDesc {
     Phys P;
     Bufs B;
     ForceArgs F;
-    int nA;  // scan tiles (256 ions)
-    int nK;  // kick tiles (256 ions)
+    int nA;  // scan tiles (BATCH_TILE ions)
+    int nK;  // kick tiles (BATCH_TILE ions)
 };
 
 // Device control block of a batched launch.

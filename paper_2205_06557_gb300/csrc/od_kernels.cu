@@ -311,6 +311,7 @@ int launch_forces_f64(const Phys& P, const Bufs& B, int after_push, cudaStream_t
 int launch_forces(const Phys& P, const Bufs& B, const ForceArgs& F, int v, cudaStream_t s)
 {
     if (P.N == 0 || (P.flags & OD_F_NO_IONION) || F.G == 0) return 0;
+    if (v < 0 || v >= num_force_variants() || (kVariants[v].sym == 2 && !F.sched)) return (int)cudaErrorInvalidValue;
     int idx = 0;
 #define OD_V(bt, ipt)                                                \
     if (v == idx++) {                                                \

@@ -458,24 +458,43 @@ __device__ __forceinline__ void sym2_unit(const float4* __restrict__ fpos, float
     for (int k = 0; k < IPT; ++k) out[k * BT] = make_float4(ax[k], ay[k], az[k], 0.f);
 }
 
-// Persistent symmetric kernel on packed FP32 pairs: contiguous ranges of tile-pair units.
-// The 8-target variants are held to 128 registers (a few spills) for one more resident
-// CTA per SM, which measured 1% faster than their natural 133.
+// Dynamic unit queue: a persistent CTA takes the next unit index from sched[0] (units
+// write fixed slots, so which CTA evaluates a unit changes no result); the last CTA to
+// finish resets both words for the next launch on the stream.
+__device__ __forceinline__ long long next_unit(unsigned long long* sched, long long& s_u)
+{
+    __syncthreads();  // every thread has read the previous index
+    if (threadIdx.x == 0) s_u = (long long)atomicAdd(sched, 1ull);
+    __syncthreads();
+    return s_u;
+}
+
+__device__ __forceinline__ void leave_queue(unsigned long long* sched)
+{
+    if (threadIdx.x == 0 && atomicAdd(sched + 1, 1ull) == gridDim.x - 1) {
+        sched[0] = 0ull;
+        sched[1] = 0ull;
+    }
+}
+
+// Persistent symmetric kernel on packed FP32 pairs: tile-pair units from the dynamic
+// queue.  The 8-target variants are held to 128 registers (a few spills) for one more
+// resident CTA per SM, which measured 1% faster than their natural 133.
 template <int BT, int IPT>
 __global__ void __launch_bounds__(BT, (IPT == 8 ? 65536 / (BT * 128) : 1)) k_forces_sym2(const float4* __restrict__ fpos, float4* __restrict__ part,
                                                     ForceArgs F)
 {
     __shared__ float s_acc[2][3][BT / 32][SYM_SUB];
     __shared__ float4 sj[BT];
-    long long u = (long long)blockIdx.x * F.U / F.G;
-    const long long u_end = (long long)(blockIdx.x + 1) * F.U / F.G;
-    if (u >= u_end) return;
-    int I, J;
-    tri_unit(u, F.JS, I, J);
-    for (; u < u_end; ++u) {
+    __shared__ long long s_u;
+    for (;;) {
+        const long long u = next_unit(F.sched, s_u);
+        if (u >= F.U) break;
+        int I, J;
+        tri_unit(u, F.JS, I, J);
         sym2_unit<BT, IPT>(fpos, part, F, I, J, s_acc, sj, J, I);
-        if (++J == F.JS) J = ++I;
     }
+    leave_queue(F.sched);
 }
 
 // One (target tile t, source chunk c) unit written to partial slot c (batched launch,
