@@ -44,9 +44,9 @@ PAIRS_PER_CLK_SM = {0: min(128 / 14, 1 / SFU_CLK_PER_PAIR), 1: min(128 / 8.5, 2 
 # that kernel on that ion count (profiles/k_forces_at_scale_200k.md and
 # profiles/k_forces_sym_at_scale_200k.md); any other kernel or size reports null until it
 # has been captured
-NCU_DRAM_BYTES = {("k_forces<256,2>", 199969): 3217152, ("k_forces_sym2<256,4>", 199969): 574284800,
-                  ("k_forces_sym<128,4>", 199969): 1197502136, ("k_forces_sym2<64,8>", 199969): 1202494720,
-                  ("k_forces_sym2<128,8>", 199969): 574913024}
+NCU_DRAM_BYTES = {("k_forces<256,2>", 199969): 3217152, ("k_forces_sym<128,4>", 199969): 1197502136,
+                  ("k_forces_sym2<64,8>", 199969): 4872704 + 1190563840,
+                  ("k_forces_sym2<128,8>", 199969): 4732672 + 567529472}
 
 
 def parse():

@@ -150,7 +150,8 @@ __device__ __forceinline__ void tri_unit(long long u, int T, int& I, int& J)
 
 // Symmetric (Newton III) all-pairs kernel: each unordered pair is evaluated once and
 // applied to both ions.  Tiles of TI = BT IPT ions; units are the tile pairs (I, J >= I)
-// in row-major order, split into contiguous ranges over the persistent blocks.
+// in row-major order, split into contiguous ranges over the persistent blocks (the packed
+// kernel k_forces_sym2 takes them from a dynamic queue instead).
 //
 // Unit (I, J > I): warp w holds 32 IPT targets of tile I (IPT per lane) and walks tile J
 // in groups of 32 sources, one per lane.  Each source travels round the warp by shuffles
