@@ -529,16 +529,29 @@ __device__ __forceinline__ void kick_body(const Phys& P, const Bufs& B, const Fo
                 const long long u0 = (long long)t * F.JS;
                 ns = owner_of(u0 + F.JS - 1, F.U, F.G) - owner_of(u0, F.U, F.G) + 1;
             }
-            // blocked sum over the slots (up to ~1000 with the symmetric kernel)
+            // blocked sum over the slots (up to ~1000 with the symmetric kernel); whole
+            // blocks of 16 issue all their loads at once, the same order of additions
+            const float4* ps = B.part + q;
+            const long long ld = F.n_pad;
             for (int s0 = 0; s0 < ns; s0 += 16) {
-                const int s1 = min(ns, s0 + 16);
                 float bx = 0.f, by = 0.f, bz = 0.f;
-#pragma unroll 8
-                for (int s = s0; s < s1; ++s) {
-                    const float4 p = __ldcs(B.part + (long long)s * F.n_pad + q);
-                    bx += p.x;
-                    by += p.y;
-                    bz += p.z;
+                if (s0 + 16 <= ns) {
+                    float4 p[16];
+#pragma unroll
+                    for (int s = 0; s < 16; ++s) p[s] = __ldcs(ps + (long long)(s0 + s) * ld);
+#pragma unroll
+                    for (int s = 0; s < 16; ++s) {
+                        bx += p[s].x;
+                        by += p[s].y;
+                        bz += p[s].z;
+                    }
+                } else {
+                    for (int s = s0; s < ns; ++s) {
+                        const float4 p = __ldcs(ps + (long long)s * ld);
+                        bx += p.x;
+                        by += p.y;
+                        bz += p.z;
+                    }
                 }
                 ax += bx;
                 ay += by;
