@@ -538,6 +538,7 @@ int replan(od_handle* h, int N)
         h->F = h->cut_on ? plan_cut(h, N) : plan_forces(N, h->variant, h->sms, h->upb, h->bps);
     }
     h->F.sched = h->d_sched;
+    h->F.n_live = (const int*)((const char*)h->B.ctrl + offsetof(Ctrl, n_cur));
     h->P.n_pad = h->F.n_pad;
     if (h->F.n_pad > h->npad_cap) return fail(h, OD_EOVERFLOW, "padded ion count exceeds the buffer");
     return ensure_part(h);

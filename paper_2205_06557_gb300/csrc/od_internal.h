@@ -140,6 +140,8 @@ struct ForceArgs {
     // dynamic unit queue of the packed symmetric and cutoff kernels: [0] next unit,
     // [1] CTAs finished (both zero between launches)
     unsigned long long* sched;
+    // live ion count (device; the plan covers the capacity under the flux rule), or null
+    const int* n_live;
 };
 
 // One run of a batched launch (od_batch.cu): its parameters, buffers and pair plan.
