@@ -520,7 +520,11 @@ __device__ __forceinline__ void kick_body(const Phys& P, const Bufs& B, const Fo
             // sorted position (cutoff: slots 0 .. degree - 1)
             int ns = F.W;
             int q = i;  // position in the pair kernel's ion order
-            if (F.cut) {
+            if (F.sym && !F.cut) {
+                // symmetric: one slot per tile; tiles from the live count on hold only
+                // dummies and their slots are not written (exact zeros)
+                ns = min(ns, (C->n_cur + F.TI - 1) / F.TI);
+            } else if (F.cut) {
                 q = F.rank[i];
                 const int t = q / F.TI;
                 ns = F.nbr_start[t + 1] - F.nbr_start[t];

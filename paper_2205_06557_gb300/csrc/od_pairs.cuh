@@ -490,21 +490,15 @@ __global__ void __launch_bounds__(BT, (IPT == 8 ? 65536 / (BT * 128) : 1)) k_for
     __shared__ float4 sj[BT];
     __shared__ long long s_u;
     // tiles from the live count on hold only far-away dummies, whose terms are exactly
-    // zero: a unit of two such tiles is skipped (no live ion reads its slots), and one
-    // whose source tile is such writes zeros to the target tile's slot
+    // zero: units that reach such a tile (J >= I) are skipped, and the kick reads only the
+    // slots of the live tiles
     const int n_live = F.n_live ? *F.n_live : F.n_pad;
     for (;;) {
         const long long u = next_unit(F.sched, s_u);
         if (u >= F.U) break;
         int I, J;
         tri_unit(u, F.JS, I, J);
-        if (I * TI >= n_live) continue;
-        if (J * TI >= n_live) {
-            float4* out = part + (long long)J * F.n_pad + I * TI + threadIdx.x;
-#pragma unroll
-            for (int k = 0; k < IPT; ++k) out[k * BT] = make_float4(0.f, 0.f, 0.f, 0.f);
-            continue;
-        }
+        if (J * TI >= n_live) continue;
         sym2_unit<BT, IPT>(fpos, part, F, I, J, s_acc, sj, J, I);
     }
     leave_queue(F.sched);

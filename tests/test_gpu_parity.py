@@ -354,3 +354,25 @@ def test_tuned_configuration_keeps_results():
     xr, _, _, ir = ref.get_ions()
     xt, _, _, it = tuned.get_ions()
     assert np.array_equal(ir, it) and np.abs(xr - xt).max() < 1e-12
+
+
+@pytest.mark.parametrize("variant", [16, 17])  # sym2<128,8>, sym2<64,8>
+def test_unit_queue_results_do_not_depend_on_the_grid(variant):
+    """The packed kernel takes its tile pairs from a queue, so the CTA that evaluates a unit
+    varies from launch to launch; each unit writes fixed slots, so every grid size gives the
+    same bits, and the queue is reset after each launch (repeated evaluations agree)."""
+    p = W.at_scale(steps=100)
+    p.update(n_ions=40000)
+    run = od.Run(p)
+    x, v, _, ids = run.get_ions()
+    accs = []
+    for bps in (0, 1, 2, 0):
+        od.od_set_force_config(run.h, variant, 8, bps)
+        for _ in range(2):
+            run.set_ions(x, v, ids, next_id=len(ids))
+            accs.append(run.get_ions()[2])
+    for a in accs[1:]:
+        assert np.array_equal(a, accs[0])
+    run.step(3)
+    assert run.counters()[13] == 3
+    run.close()
