@@ -232,9 +232,11 @@ int od_kernel_times(od_handle* h, double* ms, int64_t* launches);
  * persistent block; the symmetric variants have fixed-size units and are timed at the
  * first only) and three persistent grid sizes (CTAs per SM: the occupancy limit, 4, 2)
  * on the run's current ions, reps launches of the force evaluation plus the kick (which
- * sums the partial slots) each, keeps the fastest and writes the average ms to
- * ms[n_variants][4][3] (host, may be NULL; -1 where a setting is not timed; symmetric
- * layouts needing more than 1/8 of the free device memory are skipped).  It then
+ * sums the partial slots) each, and writes these averages in ms to ms[n_variants][4][3]
+ * (host, may be NULL; -1 where a setting is not timed; symmetric layouts needing more
+ * than 1/8 of the free device memory are skipped).  The three fastest settings are then
+ * timed again in turn, three rounds of reps launches each, and the fastest in total is
+ * kept (one of the three smallest entries of ms).  It then
  * re-evaluates the current state's forces with the chosen kernel and frees unused slot
  * memory.  Without tuning a run uses variant 0 up to 4,096 ions, 2 up to 32,768, then 15
  * while its slots fit in 16 GB (~1.05 million ions), else 3.

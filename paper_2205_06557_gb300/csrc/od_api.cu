@@ -1056,8 +1056,11 @@ int od_set_ions(od_handle* h, const double* x, const double* v, const double* a,
     OD_CK(h, cudaMemcpyAsync((char*)h->B.ctrl + offsetof(Ctrl, n_cur), &n_live, sizeof(int), cudaMemcpyHostToDevice,
                              h->stream));
     OD_CK(h, cudaStreamSynchronize(h->stream));  // n_live is a host local
+    // the step graph holds the plan by value and the plan is a function of the planned
+    // ion count (a cutoff slot resize rebuilds it in cut_fit): keep it when that is unchanged
+    const int n_plan_old = h->P.N;
     if ((rc = replan(h, plan_n(h, n)))) return rc;
-    h->graph_ok = false;
+    if (h->P.N != n_plan_old) h->graph_ok = false;
     OD_LK(h, launch_fpos(h->P, h->B, buf, h->stream));
     if ((rc = cut_fit(h))) return rc;
     // given accelerations were converted on the device above; otherwise evaluate them

@@ -491,14 +491,14 @@ __global__ void __launch_bounds__(BT, (IPT == 8 ? 65536 / (BT * 128) : 1)) k_for
     __shared__ long long s_u;
     // tiles from the live count on hold only far-away dummies, whose terms are exactly
     // zero: units that reach such a tile (J >= I) are skipped, and the kick reads only the
-    // slots of the live tiles
-    const int n_live = F.n_live ? *F.n_live : F.n_pad;
+    // slots of the live tiles.  The count is read again for every unit (a volatile load),
+    // so that it takes no register across the unit's code, which sits at the register cap.
     for (;;) {
         const long long u = next_unit(F.sched, s_u);
         if (u >= F.U) break;
         int I, J;
         tri_unit(u, F.JS, I, J);
-        if (J * TI >= n_live) continue;
+        if (F.n_live && J * TI >= *(volatile const int*)F.n_live) continue;
         sym2_unit<BT, IPT>(fpos, part, F, I, J, s_acc, sj, J, I);
     }
     leave_queue(F.sched);

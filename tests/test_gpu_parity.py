@@ -344,7 +344,8 @@ def test_tuned_configuration_keeps_results():
     ref = od.Run(p)
     tuned = od.Run(p)
     ms, v, g, b = od.od_tune(tuned.h, reps=1)
-    assert ms[v, [4, 8, 16, 32].index(g), [0, 4, 2].index(b)] == ms[ms > 0].min()
+    # the choice comes from a final round among the three fastest settings of the sweep
+    assert ms[v, [4, 8, 16, 32].index(g), [0, 4, 2].index(b)] <= np.sort(ms[ms > 0])[:3].max()
     assert od.od_get_force_config(tuned.h)[:3] == (v, g, b)
     ref.step(20)
     tuned.step(20)
