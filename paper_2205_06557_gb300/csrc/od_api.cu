@@ -725,6 +725,8 @@ void free_all(od_handle* h)
     if (h->graph) cudaGraphDestroy(h->graph);
     for (auto& e : h->ev)
         if (e) cudaEventDestroy(e);
+    for (auto& e : h->pev)
+        if (e) cudaEventDestroy(e);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
 }
 
@@ -840,6 +842,21 @@ int od_create(const od_params* p, od_handle** out)
     return OD_OK;
 }
 
+// per-kernel times of the steps recorded in the profiling ring (waits for the last one)
+int drain_profile(od_handle* h)
+{
+    OD_CK(h, cudaEventSynchronize(h->pev[5 * h->pev_used - 1]));
+    for (int s = 0; s < h->pev_used; ++s)
+        for (int k = 0; k < 4; ++k) {
+            float ms = 0.f;
+            OD_CK(h, cudaEventElapsedTime(&ms, h->pev[5 * s + k], h->pev[5 * s + k + 1]));
+            h->kms[k] += ms;
+            h->klaunch[k] += 1;
+        }
+    h->pev_used = 0;
+    return OD_OK;
+}
+
 int od_step(od_handle* h, int64_t n)
 {
     if (!h || n < 0) return fail(h, OD_EINVAL, "bad handle or step count");
@@ -866,23 +883,20 @@ int od_step(od_handle* h, int64_t n)
     for (int64_t s = 0; s < n; ++s) {
         if (direct) {
             if (h->profiling) {
-                OD_CK(h, cudaEventRecord(h->ev[0], h->stream));
+                // events around each kernel, read PROF_RING steps at a time, so that the
+                // host runs ahead of the device and leaves no gap between steps
+                cudaEvent_t* e = &h->pev[5 * h->pev_used];
+                OD_CK(h, cudaEventRecord(e[0], h->stream));
                 OD_LK(h, launch_push_scan(h->P, h->B, h->stream));
-                OD_CK(h, cudaEventRecord(h->ev[1], h->stream));
+                OD_CK(h, cudaEventRecord(e[1], h->stream));
                 OD_LK(h, launch_pairs(h, 1));
-                OD_CK(h, cudaEventRecord(h->ev[2], h->stream));
+                OD_CK(h, cudaEventRecord(e[2], h->stream));
                 OD_LK(h, launch_kick(h->P, h->B, h->F, 0, h->stream));
-                OD_CK(h, cudaEventRecord(h->ev[3], h->stream));
+                OD_CK(h, cudaEventRecord(e[3], h->stream));
                 OD_LK(h, launch_dust(h->P, h->B, 0, h->stream));
-                OD_CK(h, cudaEventRecord(h->ev[4], h->stream));
+                OD_CK(h, cudaEventRecord(e[4], h->stream));
                 if ((rc = launch_density(h))) return rc;
-                OD_CK(h, cudaEventSynchronize(h->ev[4]));
-                for (int k = 0; k < 4; ++k) {
-                    float ms = 0.f;
-                    OD_CK(h, cudaEventElapsedTime(&ms, h->ev[k], h->ev[k + 1]));
-                    h->kms[k] += ms;
-                    h->klaunch[k] += 1;
-                }
+                if (++h->pev_used == PROF_RING && (rc = drain_profile(h))) return rc;
             } else {
                 rc = launch_step(h);
                 if (rc) return rc;
@@ -891,6 +905,7 @@ int od_step(od_handle* h, int64_t n)
             OD_CK(h, cudaGraphLaunch(h->gexec, h->stream));
         }
     }
+    if (h->profiling && h->pev_used && (rc = drain_profile(h))) return rc;
     h->host_step += n;
     if (h->d_hist) h->hist_samples += n;
     return read_error_word(h);
@@ -1082,6 +1097,11 @@ int od_info(od_handle* h, double* out)
 int od_set_profiling(od_handle* h, int on)
 {
     if (!h) return fail(h, OD_EINVAL, "bad handle");
+    if (on && h->pev.empty()) {
+        h->pev.assign(5 * PROF_RING, nullptr);
+        for (auto& e : h->pev) OD_CK(h, cudaEventCreate(&e));
+    }
+    h->pev_used = 0;
     h->profiling = on != 0;
     for (int k = 0; k < 4; ++k) {
         h->kms[k] = 0.0;

@@ -9,6 +9,8 @@
 
 #include "od_internal.h"
 
+constexpr int PROF_RING = 64;  // steps per read of the profiling events
+
 struct od_handle {
     od::Phys P{};
     od::Bufs B{};
@@ -35,6 +37,8 @@ struct od_handle {
     std::string err;
     bool profiling = false;
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    std::vector<cudaEvent_t> pev;  // profiling: 5 events per step for up to PROF_RING steps
+    int pev_used = 0;              // steps recorded in pev and not yet read
     double kms[4] = {0, 0, 0, 0};
     long long klaunch[4] = {0, 0, 0, 0};
     double* d_stats = nullptr;

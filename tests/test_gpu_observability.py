@@ -116,3 +116,22 @@ def test_ion_dumps_hold_the_exact_state(tmp_path):
     assert np.array_equal(c[:, 1:4], x) and np.array_equal(c[:, 4:7], v)
     assert np.array_equal(np.loadtxt(csv, delimiter=",", skiprows=1, usecols=0, dtype=np.uint64), ids)
     run.close()
+
+
+def test_kernel_times_span_more_steps_than_the_event_ring():
+    """per-kernel profiling records events for every step and reads them 64 steps at a
+    time: a call of 70 steps and one of 5 count 75 launches of each stage, and the
+    profiled (directly launched) steps give the same bits as graph-replayed ones"""
+    p = W.tiny(steps=200)
+    prof, ref = od.Run(p), od.Run(p)
+    od.od_set_profiling(prof.h, 1)
+    prof.step(70)
+    prof.step(5)
+    ms, n = od.od_kernel_times(prof.h)
+    assert n.tolist() == [75] * 4 and (ms > 0).all()
+    od.od_set_profiling(prof.h, 0)
+    ref.step(75)
+    for a, b in zip(prof.get_ions(), ref.get_ions()):
+        assert np.array_equal(a, b)
+    prof.close()
+    ref.close()
