@@ -214,7 +214,10 @@ int od_density_read(od_handle* h, uint64_t* counts, double* density, int64_t* sa
 int od_info(od_handle* h, double* out);
 
 /* Per-kernel timing (profiling mode): when on, od_step launches kernels directly with
- * CUDA events around each and accumulates their durations. ms[4] and launches[4] for
+ * CUDA events around each and accumulates their durations, reading the events 64 steps
+ * at a time and at the end of the call (the host does not wait between steps, so the
+ * device runs them back to back; results are bit-identical to the graph replay).
+ * od_set_profiling resets the sums. od_kernel_times: ms[4] and launches[4] for
  * push+scan+inject, pair forces, kick+collide, grain update. Host arrays. */
 int od_set_profiling(od_handle* h, int on);
 int od_kernel_times(od_handle* h, double* ms, int64_t* launches);
