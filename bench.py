@@ -40,13 +40,35 @@ UNIT = "pairs/s"
 SFU_CLK_PER_PAIR = 1 / 16 + 1 / 32
 PAIRS_PER_CLK_SM = {0: min(128 / 14, 1 / SFU_CLK_PER_PAIR), 1: min(128 / 8.5, 2 / SFU_CLK_PER_PAIR),
                     2: min(128 / 8.5, 2 / SFU_CLK_PER_PAIR)}
-# dram__bytes_read.sum + dram__bytes_write.sum of one launch, from the full ncu capture of
-# that kernel on that ion count (profiles/k_forces_at_scale_200k.md and
-# profiles/k_forces_sym_at_scale_200k.md); any other kernel or size reports null until it
-# has been captured
-NCU_DRAM_BYTES = {("k_forces<256,2>", 199969): 3217152, ("k_forces_sym<128,4>", 199969): 1197502136,
-                  ("k_forces_sym2<64,8>", 199969): 4711424 + 1190526976,
-                  ("k_forces_sym2<128,8>", 199969): 4867584 + 567961600}
+KERNEL_SOURCES = ("od_pairs.cuh", "od_device.cuh", "od_internal.h", "od_kernels.cu")
+
+
+def kernel_sources_hash():
+    """sha256 (16 hex digits) of the sources the pair kernels are compiled from"""
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2205_06557_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel, n_ions):
+    """dram__bytes_read.sum + dram__bytes_write.sum of one launch of `kernel` at n_ions
+    from the table of ncu captures in profiles/dram_traffic.md, if one was taken with the
+    current kernel sources (same hash); else None"""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.md")
+    try:
+        rows = open(path).read().splitlines()
+    except OSError:
+        return None
+    want = kernel_sources_hash()
+    for r in rows:
+        c = [t.strip().strip("`") for t in r.strip().strip("|").split("|")]
+        if len(c) >= 4 and c[0] == kernel and c[1].replace(",", "").isdigit() and c[3] == want:
+            if int(c[1].replace(",", "")) == int(n_ions):
+                return int(c[2].replace(",", ""))
+    return None
 
 
 def parse():
@@ -55,8 +77,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="scale",
-                    choices=["scale", "tiny", "chain", "sweep", "warmstart", "cutoff", "production"])
+    ap.add_argument("--workload", default="chain",
+                    choices=["chain", "scale", "tiny", "sweep", "warmstart", "cutoff", "production"])
     ap.add_argument("--run-steps", type=int, default=20000)
     ap.add_argument("--max-all-pairs-log2", type=int, default=20)
     ap.add_argument("--label-steps", type=int, default=60000)
@@ -67,8 +89,10 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--pair-config", default="tuned",
-                    help="pair-kernel choice 'variant,units_per_block,ctas_per_sm' instead of the autotuner's")
+    ap.add_argument("--pair-config", default="auto",
+                    help="pair-kernel choice: 'tuned' (autotuner, cached), 'default' (the library's untuned "
+                         "choice), 'variant,units_per_block,ctas_per_sm', or 'auto' (tuned up to 250,000 ions, "
+                         "else the default)")
     return ap.parse_args()
 
 
@@ -144,8 +168,27 @@ def peaks():
         return {}
 
 
-def cpu_baseline(p, seconds):
-    """the FP64 oracle's pair forces for a sample of target ions against all ions"""
+def cpu_model():
+    """the host CPU's model name (lscpu; /proc/cpuinfo as a fallback)"""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
+def oracle_pair_rate(p, seconds):
+    """(ordered pairs/s, targets, ions, seconds, threads) of the FP64 oracle's pair forces
+    for a sample of target ions against all ions of the workload's size"""
     import oracle
 
     o = oracle.Oracle(dict(p, n_ions=1))
@@ -161,8 +204,32 @@ def cpu_baseline(p, seconds):
     t0 = time.perf_counter()
     o.forces(0, m, dust=False)
     dt = time.perf_counter() - t0
-    return {"value": m * (n - 1) / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": "FP64 oracle pair forces of %d of %d target ions against all %d ions (%.1f s)" % (m, n, n, dt)}
+    return m * (n - 1) / dt, m, n, dt, oracle.num_threads()
+
+
+def single_core_rate(workload_name, seconds):
+    """the oracle's pair rate on one host core (a child process with OMP_NUM_THREADS=1)"""
+    code = ("import sys, json; sys.path.insert(0, %r); import bench; p, _ = bench.workload(%r, 0); "
+            "print(json.dumps(bench.oracle_pair_rate(p, %r)))" % (ROOT, workload_name, float(seconds)))
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=600)
+        rate, m, n, dt, thr = json.loads(r.stdout.strip().splitlines()[-1])
+        return {"value": rate, "cores": thr, "sample": "%d of %d target ions against all %d ions (%.1f s)" % (m, n, n, dt)}
+    except (OSError, subprocess.SubprocessError, ValueError, IndexError):
+        return None
+
+
+def cpu_baseline(p, seconds, workload_name):
+    """the FP64 oracle's pair forces for a sample of target ions against all ions, on all
+    host cores (OpenMP) and on one core"""
+    rate, m, n, dt, threads = oracle_pair_rate(p, seconds)
+    out = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle", "cpu_model": cpu_model(),
+           "sample": "FP64 oracle pair forces of %d of %d target ions against all %d ions (%.1f s)" % (m, n, n, dt)}
+    one = single_core_rate(workload_name, max(2.0, seconds / 4))
+    if one:
+        out["single_core"] = dict(one, unit=UNIT)
+    return out
 
 
 def run_reference(args):
@@ -220,20 +287,21 @@ def run_ours(args):
     run = od.Run(p, stream=ctypes_stream(stream))
     N = run.N
     info = run.info()
-    if args.pair_config == "tuned":
+    mode = args.pair_config
+    if mode == "auto":
+        mode = "tuned" if N <= 250000 else "default"
+    if mode == "tuned":
         # pair-kernel autotuner (untimed; cached per device and ion count)
         tv, tg, tb, _ = od.tune_cached(run.h, "%s|N=%d" % (torch.cuda.get_device_name(local), N))
+    elif mode == "default":
+        tv, tg, tb, _ = od.od_get_force_config(run.h)  # the library's untuned choice for this N
     else:
-        tv, tg, tb = (int(t) for t in args.pair_config.split(","))
+        tv, tg, tb = (int(t) for t in mode.split(","))
         od.od_set_force_config(run.h, tv, tg, tb)
-    # L2 is not flushed: every step rewrites all positions and the pair kernel's partial
-    # slots, which outgrow the 129 MB L2 for the symmetric kernels (stated in config.l2)
-    bt, ipt, kind = od.FORCE_VARIANTS[tv]
-    ti = bt * ipt
-    n_pad = -(-N // ti) * ti
-    slot_mb = (n_pad // ti) * n_pad * 16 / 1e6 if kind else None
-    l2_note = ("not flushed: every step rewrites all positions and %.0f MB of partial slots (L2: 129 MB)" % slot_mb
-               if slot_mb else "not flushed: every step rewrites all positions and the partial slots")
+    # L2 is not flushed: every step rewrites every position (FP64 state and FP32 copy) and
+    # the inputs outgrow the 129 MB L2 from ~700,000 ions (stated in config.l2)
+    state_mb = N * 200 / 1e6
+    l2_note = "not flushed: every step reads and rewrites the whole ion state (%.0f MB; L2: 129 MB)" % state_mb
     run.step(args.warmup)
     # one call for the K timed steps: the host enqueues ahead of the device, which then runs
     # the steps back to back as in production; per-kernel events (profiling) are read every
@@ -303,13 +371,14 @@ def run_ours(args):
                    "precision": "pair forces FP32; ion state, grain sums and averages FP64",
                    "pair_kernel": {"kernel": kname, "threads": od.force_variant_shape(tv)[0], "targets_per_thread":
                                    od.force_variant_shape(tv)[1], "units_per_block": tg,
-                                   "ctas_per_sm": tb or "occupancy limit"}},
+                                   "ctas_per_sm": tb or "occupancy limit", "choice": mode}},
         "ion_steps_per_s": world * float(N) * args.steps / (t_max / 1e3),
         "wall_s_timed": wall,
         "kernel_ms_per_step": {"push_scan_inject": kms[0] / max(kn[0], 1), "pair_forces": k1_ms,
                                "kick_collide": kms[2] / max(kn[2], 1), "grain_update": kms[3] / max(kn[3], 1)},
         "roofline": {"bound": "alu", "kernel": kname, "achieved": k1_rate / 1e9, "peak": peak / 1e9,
-                     "unit": "Gpair/s", "frac": k1_rate / peak, "traffic": NCU_DRAM_BYTES.get((kname, N)),
+                     "unit": "Gpair/s", "frac": k1_rate / peak, "traffic": ncu_traffic(kname, N),
+                     "algorithmic_bytes": N * (16 + (24 if sym else 16)),
                      "peak_basis": "%d SMs x %.0f MHz x %.2f ordered pairs/clk/SM (FP32 pipe and SFU limits of %s)"
                                    % (sms, clk_max, PAIRS_PER_CLK_SM[sym],
                                       "17 FP32 + rsqrt + ex2 per unordered pair" if sym else "14 FP32 + rsqrt + ex2 per pair")},
@@ -318,7 +387,7 @@ def run_ours(args):
         "e2e": {"value": e2e_units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
     }
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(p, args.cpu_seconds)
+        line["cpu_baseline"] = cpu_baseline(p, args.cpu_seconds, args.workload)
     run.close()
     print(json.dumps(line), flush=True)
     if dist:

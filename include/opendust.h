@@ -44,6 +44,8 @@ extern "C" {
 #define OD_EOVERFLOW (-5) /* more ions than the handle's capacity */
 #define OD_ETIMEOUT (-6)  /* a device-side wait hit its iteration limit */
 #define OD_ENODEV (-7)    /* no CUDA device */
+#define OD_ERANGE (-8)    /* a pair-force partial sum left the fixed-point range of the symmetric
+                             kernels (two ions nearly coincide) */
 
 /* od_params.flags */
 #define OD_F_NO_IONION 1    /* drop the ion-ion Yukawa forces */
@@ -334,29 +336,31 @@ const char* od_last_error(const od_handle* h);
 
 /* ---- pair forces without device allocation (the paper has no counterpart) ----
  *
- * For callers that cannot allocate device memory: code recorded into a CUDA graph
- * (cudaMalloc may not be captured), latency-critical loops where an allocation
- * could synchronise the device, and host applications or plugins whose framework
- * owns all device memory and forbids allocations outside its pool.
+ * For callers that cannot allocate device memory: host applications or plugins whose
+ * framework owns every device allocation and forbids allocations outside its pool, and
+ * latency-critical loops in which a cudaMalloc (which may synchronise the device) is not
+ * acceptable.
  *
  * Computes the ion-ion Yukawa accelerations of n ions already in device memory,
  *     a_i = k * sum_{j != i} (1 + r_ij/lambda_De) exp(-r_ij/lambda_De) (x_i - x_j) / r_ij^3,
- * with the same FP32 pair arithmetic as od_step (k = q^2 / (4 pi eps0 m) for superions of
- * charge q and mass m).
+ * with the same FP32 pair arithmetic as od_step and the same FP64 correction of pairs
+ * closer than 0.005 max(1, |s|max) scaled units s = r log2(e) / lambda_De (k = q^2 /
+ * (4 pi eps0 m) for superions of charge q and mass m).
  *   x       device, [n][3] FP64 positions (m), read only
  *   n       0 .. OD_STATIC_MAX_IONS (OD_EINVAL beyond)
  *   a       device, [n][3] FP32 accelerations (m/s^2), written
  *   stream  cudaStream_t for the work (NULL = the legacy default stream); the call only
- *           queues kernels and does not wait for them
- * Scratch: a fixed array inside the library (OD_STATIC_MAX_IONS x 9 float4 = 4.5 MiB)
- * that every GPU loading the library holds until the process exits; no cudaMalloc,
- * cudaFree or allocating library routine is called.  The first call on a device looks
- * up the array's device address (once per device, with that device current); make
- * that first call before any stream capture.  Every call shares the one array and
- * leaves its contents behind; each call writes all the scratch it reads, so nothing
- * needs to start at zero.  Calls whose work overlaps on the GPU (different streams,
- * or different host threads on one device) race on the array and give wrong results:
- * serialise them. */
+ *           queues work and does not wait for it
+ * Scratch: a fixed array inside the library (about 5.1 MiB: scaled positions, 8 partial
+ * sums per ion, 65,536 close-pair cell buckets and their links, one bound word) that every
+ * GPU loading the library holds until the process exits; no cudaMalloc, cudaFree or
+ * allocating library routine is called.  The first call on a device (and the first after
+ * its context changes, e.g. after cudaDeviceReset) looks up the array's device address
+ * with that device current; make that first call before any stream capture.  Every call
+ * shares the one array and leaves its contents behind: the bound word is cleared by each
+ * call (cudaMemsetAsync), everything else it reads is written by the same call first.
+ * Calls whose work overlaps on the GPU (different streams, or different host threads on
+ * one device) race on the array and give wrong results: serialise them. */
 #define OD_STATIC_MAX_IONS 32768
 int od_pair_accel_static(const double* x, int64_t n, double lambda_De, double k, float* a, void* stream);
 

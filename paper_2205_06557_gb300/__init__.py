@@ -24,7 +24,7 @@ NCOUNT = 16
 
 OD_OK = 0
 ERRORS = {-1: "OD_EINVAL", -2: "OD_ENOMEM", -3: "OD_ECUDA", -4: "OD_ENAN", -5: "OD_EOVERFLOW",
-          -6: "OD_ETIMEOUT", -7: "OD_ENODEV"}
+          -6: "OD_ETIMEOUT", -7: "OD_ENODEV", -8: "OD_ERANGE"}
 
 F_NO_IONION = 1
 F_NO_EOUT = 2

@@ -297,6 +297,14 @@ int validate(const od_params* p, std::string& msg)
         msg = "too many ions (limit 2e8 per run)";
         return OD_EINVAL;
     }
+    {
+        // far-away padding of the pair kernels sits at 3e4 scaled units (r log2(e) / lambda_De)
+        const double lam = std::sqrt(kEPS0 * kKB * p->T_e / (p->ion_charge_number * p->n_inf * kQE * kQE));
+        if (std::sqrt(p->R * p->R + 0.25 * p->H * p->H) * 1.4426950408889634 / lam > 1e4) {
+            msg = "domain larger than 6,900 electron Debye lengths";
+            return OD_EINVAL;
+        }
+    }
     if (p->eout_grid < 0 || p->eout_grid > 400) {
         msg = "eout_grid must be in 0..400";
         return OD_EINVAL;
@@ -366,6 +374,25 @@ void derive(const od_params* p, Phys& P, od_handle* h)
     P.test_hold_tile0 = 0;
     const long long N = p->n_ions > 0 ? p->n_ions : std::llround(p->n_inf * kPI * p->R * p->R * p->H / p->weight);
     P.N = (int)N;
+    // Scaled units s = r / Ls.  Term sum of an ion at the centre of a uniform fill (its pair
+    // terms summed without signs), over the largest centred sphere of radius L: 4 pi n_s
+    // int_0^L (1 + s ln2) 2^-s ds, n_s the ions per unit scaled volume.  The fixed-point
+    // grid of the symmetric pair sums is 2^-30 of it (power of two).
+    P.ls_inv = 1.0 / Ls;
+    const double Rs = p->R / Ls, Hs = 0.5 * p->H / Ls;
+    const double n_s = (double)std::max(N, 1ll) / (kPI * p->R * p->R * p->H) * Ls * Ls * Ls;
+    const double L = std::min(Rs, Hs), ln2 = 0.69314718055994531;
+    const double ts = 4.0 * kPI * n_s * (2.0 - (2.0 + L * ln2) * std::exp2(-L)) / ln2;
+    const int K = (int)std::max(-100.0, std::min(100.0, std::floor(30.0 - std::log2(std::max(ts, 1e-300)))));
+    P.qinv = std::ldexp(1.0, -K);
+    h->qscale = (float)std::ldexp(1.0, K);
+    // close-pair correction: pairs nearer than 0.005 max(1, |s|max) scaled units (the FP32
+    // rounding of |s| moves them most relative to their separation); hashed cells 5% wider
+    const double smax = std::sqrt(Rs * Rs + Hs * Hs);
+    const double dc = 0.005 * std::max(1.0, smax);
+    P.cp_dc2 = dc * dc;
+    P.cp_hinv = (float)(1.0 / (1.05 * dc));
+    P.cp_on = !(p->flags & (OD_F_NO_IONION | OD_F_FP64_PAIRS));
     double* o = h->info;
     o[0] = lam;
     o[1] = cs;
@@ -398,7 +425,7 @@ void set_field_coeffs(Phys& P, const double* alpha, bool on)
 // App. A: potential of the uniform ion fill on the (r, z) grid, then the 15-term fit
 int build_eout(od_handle* h, const od_params* p)
 {
-    const int nx = p->eout_grid > 0 ? p->eout_grid : 40, nz = nx, nq = 48;
+    const int nx = p->eout_grid > 0 ? p->eout_grid : 40, nz = nx, nq = 64;
     const double lam = 1.0 / h->P.lam_inv;
     std::vector<double> gx, gw;
     gl_nodes(nq, gx, gw);
@@ -444,11 +471,12 @@ ForceArgs plan_forces(int N, int v, int sms, int units_per_block, int bps_cap)
     const int occ = force_blocks_per_sm(v);
     const long long gmax = (long long)sms * (bps_cap > 0 ? std::min(bps_cap, occ) : occ);
     if (fv.sym) {
-        // tile pairs (I, J >= I); units have a fixed size, so units_per_block is unused
+        // tile pairs (I, J >= I) into the fixed-point accumulators; units have a fixed
+        // size, so units_per_block is unused
         F.sym = 1;
         F.JC = F.TI;
         F.JS = n_it;
-        F.W = n_it;
+        F.W = 0;
         F.U = (long long)n_it * (n_it + 1) / 2;
         F.G = (int)std::min<long long>(gmax, F.U);
         return F;
@@ -471,22 +499,18 @@ ForceArgs plan_forces(int N, int v, int sms, int units_per_block, int bps_cap)
 }
 
 // untuned choice: ordered pairs for small runs (many small units spread over the SMs),
-// the packed symmetric kernel with 1024-ion tiles (half the pair evaluations; fastest at
-// 200k ions) above 32k ions while its partial slots (N_pad^2 / 1024 x 16 bytes) stay
-// within 16 GB, i.e. up to ~1.05 million ions
+// the packed symmetric kernel (half the pair evaluations) with 512-ion tiles above 32k ions
 int default_variant(int N)
 {
     if (N <= 4096) return 0;
     if (N <= 32768) return 2;
-    const int sym2_1024 = 15;  // k_forces_sym2<256,4>
-    const double n = (double)N + 1024.0;
-    if (n * n / 1024.0 * 16.0 <= 16.0 * (1ull << 30)) return sym2_1024;
-    return 3;
+    return 17;  // k_forces_sym2<64,8>
 }
 
 int ensure_part(od_handle* h)
 {
     const long long need = (long long)h->F.W * h->F.n_pad;
+    if (need == 0) return OD_OK;  // symmetric kernels: fixed-point accumulators only
     if (need <= h->part_cap) return OD_OK;
     if (h->B.part) cudaFree(h->B.part);
     h->B.part = nullptr;
@@ -495,8 +519,8 @@ int ensure_part(od_handle* h)
     return OD_OK;
 }
 
-// the cutoff's plan: symmetric tiles of 512 z-sorted ions, one slot per tile for every
-// ion (only the neighbouring tiles' slots are written and read)
+// the cutoff's plan: symmetric tiles of 512 z-sorted ions whose sums go to the
+// fixed-point accumulators at the ions' sorted positions
 ForceArgs plan_cut(const od_handle* h, int N)
 {
     ForceArgs F{};
@@ -507,15 +531,25 @@ ForceArgs plan_cut(const od_handle* h, int N)
     F.cut = 1;
     F.JC = F.TI;
     F.JS = T;
-    F.W = h->C.max_deg;
+    F.W = 0;
     F.U = (long long)T * (T + 1) / 2;
     F.G = h->cut_grid;
     const double ls = 1.4426950408889634 * h->P.lam_inv;
     F.cut_s0 = (float)(h->r_switch * ls);
     F.cut_inv_w = (float)(1.0 / ((h->r_cut - h->r_switch) * ls));
-    F.nbr_start = h->C.nbr_start;
     F.rank = h->C.rank;
     return F;
+}
+
+// the fixed-point accumulators, error word, unit queue and live count of the run
+void attach_sums(const od_handle* h, ForceArgs& F)
+{
+    F.psum = h->B.psum;
+    F.psum_ld = h->B.psum_ld;
+    F.qscale = h->qscale;
+    F.err = (int*)((char*)h->B.ctrl + offsetof(Ctrl, err));
+    F.sched = h->d_sched;
+    F.n_live = (const int*)((const char*)h->B.ctrl + offsetof(Ctrl, n_cur));
 }
 
 int replan(od_handle* h, int N)
@@ -537,8 +571,7 @@ int replan(od_handle* h, int N)
     } else {
         h->F = h->cut_on ? plan_cut(h, N) : plan_forces(N, h->variant, h->sms, h->upb, h->bps);
     }
-    h->F.sched = h->d_sched;
-    h->F.n_live = (const int*)((const char*)h->B.ctrl + offsetof(Ctrl, n_cur));
+    attach_sums(h, h->F);
     h->P.n_pad = h->F.n_pad;
     if (h->F.n_pad > h->npad_cap) return fail(h, OD_EOVERFLOW, "padded ion count exceeds the buffer");
     return ensure_part(h);
@@ -568,46 +601,16 @@ int read_error_word(od_handle* h)
     if (err & ERR_TIMEOUT) return fail(h, OD_ETIMEOUT, "device-side wait hit its limit (scan look-back)");
     if (err & ERR_PLACE) return fail(h, OD_EINVAL, "initial ion placement failed (grains fill the domain?)");
     if (err & ERR_OVERFLOW) return fail(h, OD_EOVERFLOW, "ion capacity exceeded");
-    if (err & ERR_CUTCAP)
-        return fail(h, OD_EOVERFLOW, "cutoff: a tile had more neighbour tiles than its partial slots (the ion density "
-                                     "became very uneven) and its step ran without ion-ion forces; load a checkpoint "
-                                     "or set the ions again, which resizes the slots");
+    if (err & ERR_RANGE)
+        return fail(h, OD_ERANGE, "a pair-force partial sum left the fixed-point range (two ions nearly coincide)");
     return OD_OK;
 }
 
-// The cutoff's slot capacity for the current positions (fpos refreshed): the tile lists
-// are built without evaluating pairs; when a tile has more neighbours than max_deg the
-// capacity grows to the largest degree plus a quarter and eight. The lists are rebuilt at
-// every evaluation, so the overflow bit of an earlier step is cleared here.
-int cut_fit(od_handle* h)
-{
-    if (!h->cut_on) return OD_OK;
-    if (h->P.N > 0 && !(h->P.flags & OD_F_NO_IONION))
-        OD_LK(h, launch_forces_cut(h->P, h->B, h->F, h->C, h->cut_grid, h->stream, 1));
-    int ov[2] = {0, 0}, err = 0;
-    char* const errp = (char*)h->B.ctrl + offsetof(Ctrl, err);
-    if (h->P.N > 0 && !(h->P.flags & OD_F_NO_IONION))
-        OD_CK(h, cudaMemcpyAsync(ov, h->C.over, sizeof(ov), cudaMemcpyDeviceToHost, h->stream));
-    OD_CK(h, cudaMemcpyAsync(&err, errp, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-    OD_CK(h, cudaStreamSynchronize(h->stream));
-    err &= ~ERR_CUTCAP;
-    OD_CK(h, cudaMemcpyAsync(errp, &err, sizeof(int), cudaMemcpyHostToDevice, h->stream));
-    OD_CK(h, cudaStreamSynchronize(h->stream));  // err is a host local
-    if (!ov[0]) return OD_OK;
-    const long long t_cap = (h->cap + h->F.TI - 1) / h->F.TI;
-    const int md = (int)std::min<long long>(t_cap, (long long)std::ceil(1.25 * ov[1]) + 8);
-    const double slot_bytes = (double)md * (double)(t_cap * h->F.TI) * sizeof(float4);
-    if (slot_bytes > 48e9)
-        return fail(h, OD_EOVERFLOW, "cutoff: the ion density is too uneven for the partial slots (" +
-                                         std::to_string(slot_bytes / 1e9) + " GB)");
-    h->C.max_deg = md;
-    h->graph_ok = false;
-    return replan(h, h->P.N);
-}
-
-// forces for the current state (creation or replaced ions)
+// forces for the current state (creation or replaced ions): FP32 positions and
+// close-pair lists rebuilt, pair forces, accelerations, Eq. 1 force
 int force_eval(od_handle* h)
 {
+    OD_LK(h, launch_fpos(h->P, h->B, (int)(h->host_step & 1), h->stream));
     OD_LK(h, launch_pairs(h, 0));
     OD_LK(h, launch_kick(h->P, h->B, h->F, 1, h->stream));
     OD_LK(h, launch_dust(h->P, h->B, 1, h->stream));
@@ -690,8 +693,8 @@ bool host_pinned(const void* p)
 void free_cut(od_handle* h)
 {
     CutBufs& C = h->C;
-    void* ptrs[] = {C.bcount, C.boff, C.bsum, C.perm, C.rank, C.fsort, C.box_lo, C.box_hi, C.nbr_start,
-                    C.nbr, C.units, C.n_units, C.cnt, C.ucnt, C.ustart, C.over};
+    void* ptrs[] = {C.bcount, C.boff, C.bsum, C.perm, C.rank, C.fsort, C.box_lo, C.box_hi,
+                    C.units, C.n_units, C.ucnt, C.ustart};
     for (void* q : ptrs) cudaFree(q);
     C = CutBufs{};
 }
@@ -706,6 +709,9 @@ void free_all(od_handle* h)
     cudaFree(h->B.acc);
     cudaFree(h->B.fpos);
     cudaFree(h->B.part);
+    cudaFree(h->B.psum);
+    cudaFree(h->B.cp_head);
+    cudaFree(h->B.cp_next);
     cudaFree(h->B.tile_status);
     cudaFree(h->B.inj);
     cudaFree(h->B.rem);
@@ -782,6 +788,17 @@ int create_impl(const od_params* p, od_handle* h)
     }
     OD_CK(h, cudaMalloc(&B.acc, sizeof(float4) * h->npad_cap));
     OD_CK(h, cudaMalloc(&B.fpos, sizeof(float4) * h->npad_cap));
+    // fixed-point pair sums [3][npad_cap] (zero between evaluations) and the close-pair
+    // cell buckets (a power of two, at least twice the capacity) and links
+    B.psum_ld = h->npad_cap;
+    OD_CK(h, cudaMalloc(&B.psum, sizeof(long long) * 3 * h->npad_cap));
+    OD_CK(h, cudaMemsetAsync(B.psum, 0, sizeof(long long) * 3 * h->npad_cap, h->stream));
+    unsigned long long nbk = 1024;
+    while (nbk < 2ull * (unsigned long long)h->cap) nbk <<= 1;
+    h->P.cp_mask = (unsigned)(nbk - 1);
+    OD_CK(h, cudaMalloc(&B.cp_head, sizeof(unsigned long long) * nbk));
+    OD_CK(h, cudaMemsetAsync(B.cp_head, 0, sizeof(unsigned long long) * nbk, h->stream));
+    OD_CK(h, cudaMalloc(&B.cp_next, sizeof(int) * h->cap));
     // one status word per scan tile: single runs scan 256-ion tiles, batch members 128
     const long long scan_tile = std::min(push_tile(), BATCH_TILE);
     const long long ntiles = (h->cap + scan_tile - 1) / scan_tile;
@@ -799,6 +816,7 @@ int create_impl(const od_params* p, od_handle* h)
     std::memset(&c0, 0, sizeof(c0));
     c0.next_id = (unsigned long long)N;
     c0.n_cur = N;
+    c0.cp_epoch = 1;  // bucket words start at epoch 0, which no build uses
     for (int k = 0; k < p->n_dust; ++k)
         c0.Q[k] = p->charge_model == OD_Q_OML ? oml_charge(p, p->dust[k].radius) : p->dust[k].q0;
     OD_CK(h, cudaMemcpyAsync(B.ctrl, &c0, sizeof(Ctrl), cudaMemcpyHostToDevice, h->stream));
@@ -1072,14 +1090,14 @@ int od_set_ions(od_handle* h, const double* x, const double* v, const double* a,
                              h->stream));
     OD_CK(h, cudaStreamSynchronize(h->stream));  // n_live is a host local
     // the step graph holds the plan by value and the plan is a function of the planned
-    // ion count (a cutoff slot resize rebuilds it in cut_fit): keep it when that is unchanged
+    // ion count: keep it when that is unchanged
     const int n_plan_old = h->P.N;
     if ((rc = replan(h, plan_n(h, n)))) return rc;
     if (h->P.N != n_plan_old) h->graph_ok = false;
-    OD_LK(h, launch_fpos(h->P, h->B, buf, h->stream));
-    if ((rc = cut_fit(h))) return rc;
-    // given accelerations were converted on the device above; otherwise evaluate them
-    if (!a && (rc = force_eval(h))) return rc;
+    // given accelerations were converted on the device above (the positions and their
+    // close-pair lists are refreshed); otherwise evaluate them
+    if (a) OD_LK(h, launch_fpos(h->P, h->B, buf, h->stream));
+    else if ((rc = force_eval(h))) return rc;
     return read_error_word(h);
 }
 
@@ -1142,6 +1160,7 @@ int od_selftest_wait_timeout(od_handle* h, int64_t polls)
     P.spin_limit = polls;
     P.test_hold_tile0 = 1;
     OD_LK(h, launch_push_scan(P, h->B, h->stream));
+    OD_LK(h, launch_cp_bump(h->B, h->stream));  // no later build reuses the epoch of the scan's lists
     OD_CK(h, cudaStreamSynchronize(h->stream));
     h->graph_ok = false;
     return read_error_word(h);

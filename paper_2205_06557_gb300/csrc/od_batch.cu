@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(BATCH_BT, 65536 / (BATCH_BT * 128))
             if (d.F.sym) {
                 int I, J;
                 tri_unit(tk.y, d.F.JS, I, J);
-                sym2_unit<BATCH_BT, IPT>(d.B.fpos, d.B.part, d.F, I, J, s_acc, sj, J, I);
+                sym2_unit<BATCH_BT, IPT>(d.B.fpos, d.F, I, J, s_acc, sj);
             } else {
                 forces_unit<BATCH_BT, IPT>(d.B.fpos, d.B.part, d.F, tk.y / d.F.JS, tk.y % d.F.JS, sj);
             }
@@ -152,12 +152,12 @@ ForceArgs batch_plan(int N, int ipt, int jc)
     F.n_pad = N == 0 ? 0 : (N + F.TI - 1) / F.TI * F.TI;
     if (F.n_pad == 0) return F;
     if (jc == 0) {
-        // symmetric tile pairs (I, J >= I), one slot per tile for every ion
+        // symmetric tile pairs (I, J >= I) into the fixed-point accumulators
         const int T = F.n_pad / F.TI;
         F.sym = 1;
         F.JC = F.TI;
         F.JS = T;
-        F.W = T;
+        F.W = 0;
         F.U = (long long)T * (T + 1) / 2;
         F.G = (int)F.U;
         return F;

@@ -64,6 +64,7 @@ int batch_build(od_batch* b)
     for (int r = 0; r < R; ++r) {
         od_handle* h = b->runs[r];
         h->F = batch_plan(h->P.N, b->ipt, b->jc);
+        attach_sums(h, h->F);
         h->P.n_pad = h->F.n_pad;
         if (h->F.n_pad > h->npad_cap) return bfail(b, OD_EOVERFLOW, "padded ion count exceeds a run's buffer");
         int rc = ensure_part(h);

@@ -20,6 +20,15 @@ namespace host {
 static const int kTuneGrains[4] = {4, 8, 16, 32};
 static const int kTuneBps[3] = {0, 4, 2};  // persistent CTAs per SM: 0 = occupancy limit
 
+// close-pair correction on when the FP32 ion-ion kernels run, and under the cutoff only
+// while the correction distance lies inside the plain (unswitched) zone
+void set_close_pairs(od_handle* h)
+{
+    const double ls = 1.4426950408889634 * h->P.lam_inv;
+    h->P.cp_on = !(h->P.flags & (OD_F_NO_IONION | OD_F_FP64_PAIRS)) &&
+                 (!h->cut_on || h->r_switch * ls * h->r_switch * ls >= h->P.cp_dc2);
+}
+
 int apply_force_config(od_handle* h, int variant, int upb, int bps)
 {
     h->variant = variant;
@@ -47,15 +56,14 @@ int od_set_cutoff(od_handle* h, double r_cut, double r_switch)
     if (!std::isfinite(r_cut) || !std::isfinite(r_switch)) return fail(h, OD_EINVAL, "cutoff: non-finite distance");
     OD_CK(h, cudaStreamSynchronize(h->stream));
     int rc;
-    const int buf = (int)(h->host_step & 1);
     if (r_cut <= 0.0) {
         if (!h->cut_on) return OD_OK;
         h->cut_on = false;
         h->r_cut = h->r_switch = 0.0;
         free_cut(h);
+        set_close_pairs(h);
         if ((rc = replan(h, h->P.N))) return rc;
         h->graph_ok = false;
-        OD_LK(h, launch_fpos(h->P, h->B, buf, h->stream));
         if ((rc = force_eval(h))) return rc;
         OD_CK(h, cudaStreamSynchronize(h->stream));
         return read_error_word(h);
@@ -72,15 +80,6 @@ int od_set_cutoff(od_handle* h, double r_cut, double r_switch)
     int nslab = (int)std::min(65536.0, std::max(1.0, std::ceil(h->P.H / (r_cut / 8.0))));
     while ((long long)nslab * nblk > (64ll << 20) && nslab > 1) nslab = (nslab + 1) / 2;
     const double w = h->P.H / nslab;
-    // slot capacity: the tiles within the cutoff plus two tile extents, for a uniform
-    // density, with a margin of half again
-    const double ext = 2.0 * std::max(w, h->P.H * TI / std::max(1.0, (double)h->P.N));
-    const double deg = T * std::min(1.0, (2.0 * r_cut + 2.0 * ext) / h->P.H) + 3.0;
-    const int max_deg = (int)std::min<double>(T, std::ceil(1.5 * deg) + 8.0);
-    const double slot_bytes = (double)max_deg * npad_max * sizeof(float4);
-    if (slot_bytes > 48e9)
-        return fail(h, OD_EINVAL, "cutoff: the partial slots would need " + std::to_string(slot_bytes / 1e9) +
-                                      " GB (cutoff too long for this domain)");
     free_cut(h);
     CutBufs& C = h->C;
     const double ls = 1.4426950408889634 * h->P.lam_inv;
@@ -91,8 +90,6 @@ int od_set_cutoff(od_handle* h, double r_cut, double r_switch)
     C.rc2_tile = (float)(rcs * rcs);
     const double rss = r_switch * ls * (1.0 - 1e-5);  // plain units: never skip a switched pair
     C.rs2_tile = (float)(rss * rss);
-    C.max_deg = max_deg;
-    C.err = (int*)((char*)h->B.ctrl + offsetof(Ctrl, err));
     const long long M = (long long)nslab * nblk;
     const long long nchunk = (M + 8191) / 8192;
     OD_CK(h, cudaMalloc(&C.bcount, sizeof(int) * M));
@@ -103,23 +100,18 @@ int od_set_cutoff(od_handle* h, double r_cut, double r_switch)
     OD_CK(h, cudaMalloc(&C.fsort, sizeof(float4) * npad_max));
     OD_CK(h, cudaMalloc(&C.box_lo, sizeof(float4) * T));
     OD_CK(h, cudaMalloc(&C.box_hi, sizeof(float4) * T));
-    OD_CK(h, cudaMalloc(&C.nbr_start, sizeof(int) * (T + 1)));
-    OD_CK(h, cudaMalloc(&C.nbr, sizeof(int) * (size_t)T * T));
-    OD_CK(h, cudaMalloc(&C.units, sizeof(int4) * ((size_t)T * (T + 1) / 2)));
+    OD_CK(h, cudaMalloc(&C.units, sizeof(int2) * ((size_t)T * (T + 1) / 2)));
     OD_CK(h, cudaMalloc(&C.n_units, sizeof(int)));
-    OD_CK(h, cudaMalloc(&C.cnt, sizeof(int) * T));
     OD_CK(h, cudaMalloc(&C.ucnt, sizeof(int) * T));
     OD_CK(h, cudaMalloc(&C.ustart, sizeof(int) * T));
-    OD_CK(h, cudaMalloc(&C.over, 2 * sizeof(int)));
     h->cut_on = true;
     h->r_cut = r_cut;
     h->r_switch = r_switch;
     h->cut_grid = h->sms * cut_blocks_per_sm(2);
+    set_close_pairs(h);
     if ((rc = replan(h, h->P.N))) return rc;
     OD_LK(h, launch_cut_dummies(C, h->P.N, h->F.n_pad, h->stream));
-    OD_LK(h, launch_fpos(h->P, h->B, buf, h->stream));
     h->graph_ok = false;
-    if ((rc = cut_fit(h))) return rc;
     if ((rc = force_eval(h))) return rc;
     OD_CK(h, cudaStreamSynchronize(h->stream));
     return read_error_word(h);
@@ -160,26 +152,18 @@ int od_tune(od_handle* h, int reps, double* ms, int* best_variant, int* best_upb
         int v, g, b;
     };
     std::vector<Timed> timed;
-    size_t free_b = 0, total_b = 0;
-    OD_CK(h, cudaMemGetInfo(&free_b, &total_b));
-    const double slot_budget = (double)(free_b + sizeof(float4) * (size_t)h->part_cap) / 8.0;
     for (int v = 0; v < nv; ++v)
         for (int g = 0; g < 4; ++g)
             for (int c = 0; c < 3; ++c) {
                 if (kTuneBps[c] >= force_blocks_per_sm(v)) continue;  // no cap below the occupancy limit
                 const ForceVariant fv = force_variant(v);
-                if (fv.sym) {
-                    if (g > 0) continue;  // fixed-size units: one grain setting
-                    // one partial slot per tile for every ion: skip layouts that would take
-                    // more than an eighth of the device memory
-                    const double ti = fv.BT * fv.IPT, np = std::ceil(h->P.N / ti) * ti;
-                    if (np / ti * np * sizeof(float4) > slot_budget) continue;
-                }
+                if (fv.sym && g > 0) continue;  // fixed-size units: one grain setting
                 int rc = apply_force_config(h, v, kTuneGrains[g], kTuneBps[c]);
                 if (rc) return rc;
-                // the kick is timed too: it sums every ion's partial slots, one per tile
-                // for the symmetric kernel
+                // the kick is timed too: it sums the ordered kernel's partial slots, or reads
+                // and clears the symmetric kernels' fixed-point sums
                 OD_LK(h, launch_forces(h->P, h->B, h->F, h->variant, h->stream));
+                OD_LK(h, launch_kick(h->P, h->B, h->F, 1, h->stream));
                 OD_CK(h, cudaEventRecord(h->ev[0], h->stream));
                 for (int r = 0; r < reps; ++r) {
                     OD_LK(h, launch_forces(h->P, h->B, h->F, h->variant, h->stream));
@@ -203,6 +187,7 @@ int od_tune(od_handle* h, int reps, double* ms, int* best_variant, int* best_upb
             int rc = apply_force_config(h, timed[f].v, timed[f].g, timed[f].b);
             if (rc) return rc;
             OD_LK(h, launch_forces(h->P, h->B, h->F, h->variant, h->stream));
+            OD_LK(h, launch_kick(h->P, h->B, h->F, 1, h->stream));
             OD_CK(h, cudaEventRecord(h->ev[0], h->stream));
             for (int r = 0; r < reps; ++r) {
                 OD_LK(h, launch_forces(h->P, h->B, h->F, h->variant, h->stream));
@@ -224,7 +209,7 @@ int od_tune(od_handle* h, int reps, double* ms, int* best_variant, int* best_upb
     int rc = apply_force_config(h, bv, bg, bb);
     if (rc) return rc;
     // give back partial-slot memory beyond what the chosen layout needs
-    if (h->part_cap > 2 * (long long)h->F.W * h->F.n_pad) {
+    if (h->part_cap > 2 * (long long)h->F.W * h->F.n_pad && h->part_cap > 0) {
         OD_CK(h, cudaStreamSynchronize(h->stream));
         cudaFree(h->B.part);
         h->B.part = nullptr;

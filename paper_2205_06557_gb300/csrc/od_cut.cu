@@ -8,14 +8,14 @@
 //      inside a slab is the ion order (deterministic);
 //   2. the sorted positions are cut into tiles of TI ions; each tile gets the bounding
 //      box of its ions;
-//   3. warps list, for every tile, the tiles whose boxes come closer than the cutoff
-//      (neighbour lists, CSR) and the tile pairs (I, J >= I) among them;
+//   3. warps list, for every tile I, the tiles J >= I whose boxes come closer than the
+//      cutoff (the tile pairs to evaluate);
 //   4. persistent CTAs evaluate those tile pairs with the symmetric packed-pair unit of
 //      the all-pairs kernel and the switched pair coefficient (the plain one where the
 //      two boxes lie wholly inside the switching distance); a pair beyond the cutoff
-//      inside a listed tile pair contributes exactly zero;
-//   5. the kick sums, for ion i, the slots of the neighbours of the tile that holds its
-//      sorted position.
+//      inside a listed tile pair contributes exactly zero; the sums go to the fixed-point
+//      accumulators at the ions' sorted positions;
+//   5. the kick reads, for ion i, the accumulator of its sorted position.
 // Nothing is read back to the host, so the step stays one CUDA graph.
 #include <algorithm>
 #include <cmath>
@@ -196,134 +196,72 @@ __device__ __forceinline__ float boxes_far2(float4 la, float4 ha, float4 lb, flo
     return fmaf(fx, fx, fmaf(fy, fy, fz * fz));
 }
 
-// Neighbour lists (CSR, ascending) and tile pairs (I, J >= I) of the tiles whose boxes
-// come closer than the cutoff, with the slot each side of a pair writes (the position of
-// the other tile in its list).  One warp per tile in every pass; T <= CUT_MAX_TILES.
-// A tile with more neighbours than max_deg slots empties the lists (no pair is
-// evaluated, the kick reads nothing) and raises ERR_CUTCAP: the step reports the error
-// instead of writing past the slots.
+// Tile pairs (I, J >= I) of the tiles whose boxes come closer than the cutoff, in row
+// order and ascending J within a row.  One warp per tile in both passes; T <= CUT_MAX_TILES.
 
-// pass 1: neighbours and tile pairs (J >= I) per tile
+// pass 1: tile pairs (J >= I) per tile
 __global__ void k_cut_count(const float4* __restrict__ lo, const float4* __restrict__ hi, int T, float rc2,
-                            int* __restrict__ cnt, int* __restrict__ ucnt)
+                            int* __restrict__ ucnt)
 {
     const int I = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (I >= T) return;
     const float4 la = lo[I], ha = hi[I];
-    int n = 0, nu = 0;
-    for (int J = lane; J < T; J += 32)
-        if (tiles_meet(la, ha, lo[J], hi[J], rc2)) {
-            ++n;
-            nu += J >= I;
-        }
+    int nu = 0;
+    for (int J = I + lane; J < T; J += 32) nu += tiles_meet(la, ha, lo[J], hi[J], rc2);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        n += __shfl_xor_sync(0xffffffffu, n, o);
-        nu += __shfl_xor_sync(0xffffffffu, nu, o);
-    }
-    if (lane == 0) {
-        cnt[I] = n;
-        ucnt[I] = nu;
-    }
+    for (int o = 16; o > 0; o >>= 1) nu += __shfl_xor_sync(0xffffffffu, nu, o);
+    if (lane == 0) ucnt[I] = nu;
 }
 
-// pass 2 (one CTA of 1024): exclusive scans, list starts, unit starts and count, overflow
-__global__ void __launch_bounds__(1024) k_cut_offsets(const int* __restrict__ cnt, const int* __restrict__ ucnt, int T,
-                                                      int max_deg, int* __restrict__ nbr_start,
-                                                      int* __restrict__ ustart, int* __restrict__ n_units,
-                                                      int* __restrict__ over, int* __restrict__ err)
+// pass 2 (one CTA of 1024): exclusive scan of the counts, unit starts and unit count
+__global__ void __launch_bounds__(1024) k_cut_offsets(const int* __restrict__ ucnt, int T, int* __restrict__ ustart,
+                                                      int* __restrict__ n_units)
 {
     __shared__ int s_w[32];
-    __shared__ int s_over, s_max;
-    if (threadIdx.x == 0) s_over = s_max = 0;
-    __syncthreads();
     constexpr int PER = CUT_MAX_TILES / 1024;
     const int base = threadIdx.x * PER;
-    int v[PER], u[PER], sv = 0, su = 0, vmax = 0;
+    int u[PER], su = 0;
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
-        v[k] = base + k < T ? cnt[base + k] : 0;
         u[k] = base + k < T ? ucnt[base + k] : 0;
-        if (v[k] > max_deg) s_over = 1;
-        vmax = max(vmax, v[k]);
-        sv += v[k];
         su += u[k];
     }
-    atomicMax(&s_max, vmax);
-    int tv, tu;
-    int rv = block_excl_scan(sv, s_w, tv);
+    int tu;
     int ru = block_excl_scan(su, s_w, tu);
-    const bool ov = s_over != 0;
 #pragma unroll
     for (int k = 0; k < PER; ++k)
         if (base + k < T) {
-            nbr_start[base + k] = ov ? 0 : rv;
             ustart[base + k] = ru;
-            rv += v[k];
             ru += u[k];
         }
-    if (threadIdx.x == 0) {
-        nbr_start[T] = ov ? 0 : tv;
-        *n_units = ov ? 0 : tu;
-        over[0] = ov ? 1 : 0;
-        over[1] = s_max;
-        if (ov) atomicOr(err, ERR_CUTCAP);
-    }
+    if (threadIdx.x == 0) *n_units = tu;
 }
 
-// pass 3: the neighbour lists in ascending order (ballot prefix per group of 32)
-__global__ void k_cut_fill(const float4* __restrict__ lo, const float4* __restrict__ hi, int T, float rc2,
-                           const int* __restrict__ nbr_start, const int* __restrict__ over, int* __restrict__ nbr)
+// pass 3: the tile pairs (ballot prefix per group of 32) with the plain flag
+__global__ void k_cut_fill(const float4* __restrict__ lo, const float4* __restrict__ hi, int T, float rc2, float rs2,
+                           const int* __restrict__ ustart, int2* __restrict__ units)
 {
     const int I = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (I >= T || *over) return;
+    if (I >= T) return;
     const float4 la = lo[I], ha = hi[I];
-    int k = nbr_start[I];
-    for (int J0 = 0; J0 < T; J0 += 32) {
+    int k = ustart[I];
+    for (int J0 = I; J0 < T; J0 += 32) {
         const int J = J0 + lane;
         const bool m = J < T && tiles_meet(la, ha, lo[J], hi[J], rc2);
         const unsigned mask = __ballot_sync(0xffffffffu, m);
-        if (m) nbr[k + __popc(mask & ((1u << lane) - 1u))] = J;
-        k += __popc(mask);
-    }
-}
-
-// pass 4: tile pairs (I, J >= I) with their slots: J's position in I's list, I's position
-// in J's list by binary search (ascending), and the plain flag
-__global__ void k_cut_units(const float4* __restrict__ lo, const float4* __restrict__ hi, int T, float rs2,
-                            const int* __restrict__ nbr_start, const int* __restrict__ nbr,
-                            const int* __restrict__ ustart, const int* __restrict__ over, int4* __restrict__ units)
-{
-    const int I = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (I >= T || *over) return;
-    const int k0 = nbr_start[I], k1 = nbr_start[I + 1];
-    const float4 la = lo[I], ha = hi[I];
-    int ku = ustart[I];
-    for (int kb = k0; kb < k1; kb += 32) {
-        const int k = kb + lane;
-        const int J = k < k1 ? nbr[k] : -1;
-        const bool m = J >= I;
-        const unsigned mask = __ballot_sync(0xffffffffu, m);
         if (m) {
-            int a = nbr_start[J], c = nbr_start[J + 1];
-            while (a < c) {
-                const int mid = (a + c) >> 1;
-                if (nbr[mid] < I) a = mid + 1;
-                else c = mid;
-            }
             const bool plain = boxes_far2(la, ha, lo[J], hi[J]) < rs2;
-            units[ku + __popc(mask & ((1u << lane) - 1u))] =
-                make_int4(I, J, k - k0, (a - nbr_start[J]) | (plain ? CUT_PLAIN : 0));
+            units[k + __popc(mask & ((1u << lane) - 1u))] = make_int2(I, J | (plain ? CUT_PLAIN : 0));
         }
-        ku += __popc(mask);
+        k += __popc(mask);
     }
 }
 
 // persistent CTAs over the listed tile pairs (their number is read on the device)
 template <int BT, int IPT>
-__global__ void __launch_bounds__(BT, (IPT == 8 ? 65536 / (BT * 128) : 1)) k_forces_cut(const float4* __restrict__ fsort, float4* __restrict__ part,
-                                                   ForceArgs F, const int4* __restrict__ units,
-                                                   const int* __restrict__ n_units)
+__global__ void __launch_bounds__(BT, (IPT == 8 ? 65536 / (BT * 128) : 1))
+    k_forces_cut(const float4* __restrict__ fsort, ForceArgs F, const int2* __restrict__ units,
+                 const int* __restrict__ n_units)
 {
     __shared__ float s_acc[2][3][BT / 32][SYM_SUB];
     __shared__ float4 sj[BT];
@@ -332,11 +270,11 @@ __global__ void __launch_bounds__(BT, (IPT == 8 ? 65536 / (BT * 128) : 1)) k_for
     for (;;) {
         const long long u = next_unit(F.sched, s_u);
         if (u >= U) break;
-        const int4 t = units[u];  // (I, J, slot of J in I's list, slot of I in J's list | flag)
-        if (t.w & CUT_PLAIN)
-            sym2_unit<BT, IPT, false>(fsort, part, F, t.x, t.y, s_acc, sj, t.z, t.w & (CUT_PLAIN - 1));
+        const int2 t = units[u];  // (I, J | plain flag)
+        if (t.y & CUT_PLAIN)
+            sym2_unit<BT, IPT, false>(fsort, F, t.x, t.y & (CUT_PLAIN - 1), s_acc, sj);
         else
-            sym2_unit<BT, IPT, true>(fsort, part, F, t.x, t.y, s_acc, sj, t.z, t.w);
+            sym2_unit<BT, IPT, true>(fsort, F, t.x, t.y, s_acc, sj);
     }
     leave_queue(F.sched);
 }
@@ -357,8 +295,7 @@ int launch_cut_dummies(const CutBufs& C, int N, int n_pad, cudaStream_t s)
     return ckc(cudaGetLastError());
 }
 
-int launch_forces_cut(const Phys& P, const Bufs& B, const ForceArgs& F, const CutBufs& C, int grid, cudaStream_t s,
-                      int lists_only)
+int launch_forces_cut(const Phys& P, const Bufs& B, const ForceArgs& F, const CutBufs& C, int grid, cudaStream_t s)
 {
     const int N = P.N;
     if (N == 0 || (P.flags & OD_F_NO_IONION)) return 0;
@@ -380,15 +317,13 @@ int launch_forces_cut(const Phys& P, const Bufs& B, const ForceArgs& F, const Cu
     const int T = F.n_pad / F.TI;
     k_cut_boxes<<<T, 256, 0, s>>>(C.fsort, N, F.TI, C.box_lo, C.box_hi);
     const int wb = (T + 7) / 8;  // 8 warps per CTA, one per tile
-    k_cut_count<<<wb, 256, 0, s>>>(C.box_lo, C.box_hi, T, C.rc2_tile, C.cnt, C.ucnt);
-    k_cut_offsets<<<1, 1024, 0, s>>>(C.cnt, C.ucnt, T, C.max_deg, C.nbr_start, C.ustart, C.n_units, C.over, C.err);
-    if (lists_only) return ckc(cudaGetLastError());
-    k_cut_fill<<<wb, 256, 0, s>>>(C.box_lo, C.box_hi, T, C.rc2_tile, C.nbr_start, C.over, C.nbr);
-    k_cut_units<<<wb, 256, 0, s>>>(C.box_lo, C.box_hi, T, C.rs2_tile, C.nbr_start, C.nbr, C.ustart, C.over, C.units);
+    k_cut_count<<<wb, 256, 0, s>>>(C.box_lo, C.box_hi, T, C.rc2_tile, C.ucnt);
+    k_cut_offsets<<<1, 1024, 0, s>>>(C.ucnt, T, C.ustart, C.n_units);
+    k_cut_fill<<<wb, 256, 0, s>>>(C.box_lo, C.box_hi, T, C.rc2_tile, C.rs2_tile, C.ustart, C.units);
     if (F.TI == 1024)
-        k_forces_cut<256, 4><<<grid, 256, 0, s>>>(C.fsort, B.part, F, C.units, C.n_units);
+        k_forces_cut<256, 4><<<grid, 256, 0, s>>>(C.fsort, F, C.units, C.n_units);
     else  // 512-ion tiles: 64 threads x 8 targets
-        k_forces_cut<64, 8><<<grid, 64, 0, s>>>(C.fsort, B.part, F, C.units, C.n_units);
+        k_forces_cut<64, 8><<<grid, 64, 0, s>>>(C.fsort, F, C.units, C.n_units);
     return ckc(cudaGetLastError());
 }
 

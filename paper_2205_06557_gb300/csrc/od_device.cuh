@@ -183,6 +183,161 @@ __device__ __forceinline__ float4 scaled(const Phys& P, double x, double y, doub
 
 __device__ __forceinline__ double rnd32(double v) { return (double)(float)v; }
 
+// ------------------------------------------------ close-pair cell lists
+// The pair kernels see positions rounded to FP32 (scaled units s), which moves a pair's
+// separation d by up to ~|s| 2^-24 and its 1/d^2 term by three times that relative to d:
+// for the rare pairs much closer than the mean spacing this is the dominant error of an
+// ion's force.  Every live ion is entered, at the end of the push (or whenever the FP32
+// positions are rewritten), into a hashed grid of cells at least as wide as the
+// correction distance; the kick walks the 27 cells around each ion and replaces the
+// FP32-position value of every pair closer than that distance by its FP64 value.
+// A bucket word is (epoch << 32) | first ion; entries of another epoch read as empty, so
+// the grid is never cleared.  Ctrl::cp_epoch is the epoch of the last complete build
+// (the one the kick reads); a build enters its ions under the next epoch and publishes it
+// when it is complete, so no two builds share an epoch.
+__device__ __forceinline__ int cp_cell(float s, float hinv) { return __float2int_rd(s * hinv); }
+
+__device__ __forceinline__ unsigned cp_bucket(int cx, int cy, int cz, unsigned mask)
+{
+    return ((unsigned)cx * 73856093u ^ (unsigned)cy * 19349663u ^ (unsigned)cz * 83492791u) & mask;
+}
+
+__device__ __forceinline__ unsigned cp_next_epoch(unsigned e) { return e + 1u == 0u ? 1u : e + 1u; }
+
+__device__ __forceinline__ void cp_insert(unsigned long long* head, int* next, unsigned mask, float hinv, unsigned epoch,
+                                          int d, float4 f)
+{
+    const unsigned b = cp_bucket(cp_cell(f.x, hinv), cp_cell(f.y, hinv), cp_cell(f.z, hinv), mask);
+    const unsigned long long old = atomicExch(head + b, ((unsigned long long)epoch << 32) | (unsigned)d);
+    next[d] = (unsigned)(old >> 32) == epoch ? (int)(unsigned)old : -1;
+}
+
+// FP64 pair term of the ion-ion sum in scaled units for d = s_j - s_i:
+// d (1 + s ln2) 2^-s / s^3 with s = |d|
+__device__ __forceinline__ void pair_term_f64(double dx, double dy, double dz, double& tx, double& ty, double& tz)
+{
+    const double s2 = dx * dx + dy * dy + dz * dz;
+    const double s = sqrt(s2);
+    const double c = (1.0 + s * 0.69314718055994531) * exp2(-s) / (s2 * s);
+    tx = c * dx;
+    ty = c * dy;
+    tz = c * dz;
+}
+
+// Close-pair correction of target i, in scaled units: the sum over ions j with
+// |s_j - s_i| < sqrt(dc2) (FP64 positions) of T(d) - T(d~), T the pair term, d the FP64
+// separation and d~ = fpos_j - fpos_i the separation the FP32 kernels used.  The sum is
+// made order-independent (the lists' order depends on the atomics that built them): the
+// terms are rounded to a common power-of-two grid set by the largest of them and added as
+// integers.  pos(j, x, y, z) gives the FP64 (unscaled) position of ion j; at most
+// CP_KEEP close pairs are kept for the second pass, more are found again.
+constexpr int CP_KEEP = 4;
+
+template <class PosF>
+__device__ void close_pair_corr(const unsigned long long* __restrict__ head, const int* __restrict__ next,
+                                const float4* __restrict__ fpos, unsigned mask, float hinv, double dc2,
+                                unsigned epoch, int n_live, double ls_inv, int i, double xi, double yi, double zi,
+                                PosF pos, double& cx, double& cy, double& cz)
+{
+    const float4 fi = fpos[i];
+    const int c0x = cp_cell(fi.x, hinv), c0y = cp_cell(fi.y, hinv), c0z = cp_cell(fi.z, hinv);
+    const double sxi = xi * ls_inv, syi = yi * ls_inv, szi = zi * ls_inv;
+    int keep[CP_KEEP];
+    int nclose = 0;
+    double big = 0.0;
+    // pass 1 (pass 2 only when more than CP_KEEP pairs were found): find the close pairs
+    // and the largest correction component; pass 2 adds them on the integer grid
+    long long qx = 0, qy = 0, qz = 0;
+    double grid = 0.0;
+    for (int pass = 0; pass < 2; ++pass) {
+        if (pass == 1) {
+            if (nclose == 0) break;
+            int e;
+            frexp(big, &e);
+            grid = ldexp(1.0, 52 - e);  // |term| * grid < 2^52: up to 2^11 terms without overflow
+        }
+        if (pass == 1 && nclose <= CP_KEEP) {
+            for (int k = 0; k < nclose; ++k) {
+                const int j = keep[k];
+                double xj, yj, zj;
+                pos(j, xj, yj, zj);
+                const float4 fj = fpos[j];
+                double t0x, t0y, t0z, t1x, t1y, t1z;
+                pair_term_f64(xj * ls_inv - sxi, yj * ls_inv - syi, zj * ls_inv - szi, t0x, t0y, t0z);
+                pair_term_f64((double)fj.x - (double)fi.x, (double)fj.y - (double)fi.y, (double)fj.z - (double)fi.z,
+                              t1x, t1y, t1z);
+                qx += __double2ll_rn((t0x - t1x) * grid);
+                qy += __double2ll_rn((t0y - t1y) * grid);
+                qz += __double2ll_rn((t0z - t1z) * grid);
+            }
+            break;
+        }
+        int found = 0;
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int cx_ = c0x + dx, cy_ = c0y + dy, cz_ = c0z + dz;
+                    const unsigned long long hw = head[cp_bucket(cx_, cy_, cz_, mask)];
+                    if ((unsigned)(hw >> 32) != epoch) continue;
+                    int j = (int)(unsigned)hw;
+                    for (int guard = 0; j >= 0 && j < n_live && guard < n_live; ++guard, j = next[j]) {
+                        if (j == i) continue;
+                        const float4 fj = fpos[j];
+                        if (cp_cell(fj.x, hinv) != cx_ || cp_cell(fj.y, hinv) != cy_ || cp_cell(fj.z, hinv) != cz_)
+                            continue;  // another cell sharing the bucket
+                        double xj, yj, zj;
+                        pos(j, xj, yj, zj);
+                        const double ex = xj * ls_inv - sxi, ey = yj * ls_inv - syi, ez = zj * ls_inv - szi;
+                        if (!(ex * ex + ey * ey + ez * ez < dc2)) continue;
+                        double t0x, t0y, t0z, t1x, t1y, t1z;
+                        pair_term_f64(ex, ey, ez, t0x, t0y, t0z);
+                        pair_term_f64((double)fj.x - (double)fi.x, (double)fj.y - (double)fi.y,
+                                      (double)fj.z - (double)fi.z, t1x, t1y, t1z);
+                        if (pass == 0) {
+                            big = fmax(big, fmax(fabs(t0x - t1x), fmax(fabs(t0y - t1y), fabs(t0z - t1z))));
+                            if (found < CP_KEEP) keep[found] = j;
+                            ++found;
+                        } else {
+                            qx += __double2ll_rn((t0x - t1x) * grid);
+                            qy += __double2ll_rn((t0y - t1y) * grid);
+                            qz += __double2ll_rn((t0z - t1z) * grid);
+                        }
+                    }
+                }
+        if (pass == 0) nclose = found;
+    }
+    if (nclose == 0 || !(big > 0.0)) {
+        cx = cy = cz = 0.0;
+        return;
+    }
+    cx = (double)qx / grid;
+    cy = (double)qy / grid;
+    cz = (double)qz / grid;
+}
+
+// ------------------------------------------------ fixed-point pair sums
+// A symmetric unit adds its FP32 partial sum v of ion q as round(v 2^K) to a 64-bit
+// integer (red.global.add): integer addition is associative, so the total does not depend
+// on which CTA evaluates which unit or in what order.  |v 2^K| must stay below 2^60
+// (K is set per run from the expected term sum, ~2^30 below it); otherwise ERR_RANGE.
+__device__ __forceinline__ void fixed_add(long long* a, float v, float qscale, int* err)
+{
+    float t = v * qscale;
+    if (!(fabsf(t) < 1.152921504606847e18f)) {
+        atomicOr(err, t != t ? ERR_NAN : ERR_RANGE);
+        t = 0.f;
+    }
+    atomicAdd((unsigned long long*)a, (unsigned long long)__float2ll_rn(t));
+}
+
+__device__ __forceinline__ void fixed_add3(long long* acc, long long ld, long long q, float vx, float vy, float vz,
+                                           float qscale, int* err)
+{
+    fixed_add(acc + q, vx, qscale, err);
+    fixed_add(acc + ld + q, vy, qscale, err);
+    fixed_add(acc + 2 * ld + q, vz, qscale, err);
+}
+
 // Number of superions injected in step sn under the flux rule: Poisson with mean lam,
 // split into chunks of at most 64, each drawn by inversion (summing e^-l l^x / x! in
 // increasing x until the sum reaches one uniform); uniform j of the step is word j mod 4
@@ -237,6 +392,9 @@ __device__ __forceinline__ void push_scan_body(const Phys& P, const Bufs& B, int
     // ions alive at the start of the step (only the last tile, after every other tile
     // has finished, writes the new count)
     const int n_live = *(volatile int*)&C->n_cur;
+    // this build of the close-pair lists takes the epoch after the last published one; the
+    // last tile publishes it when every tile has entered its ions
+    const unsigned cp_ep = cp_next_epoch(*(volatile unsigned*)&C->cp_epoch);
     if (threadIdx.x == 0) s_tile = given_tile >= 0 ? (unsigned)given_tile : atomicAdd(&C->tile_counter, 1u);
     __syncthreads();
     const int tile = (int)s_tile;
@@ -380,7 +538,9 @@ __device__ __forceinline__ void push_scan_body(const Phys& P, const Bufs& B, int
             V[cap + d] = vy;
             V[2 * cap + d] = vz;
             B.id[dst][d] = id;
-            B.fpos[d] = scaled(P, x, y, z, ls_inv);
+            const float4 f = scaled(P, x, y, z, ls_inv);
+            B.fpos[d] = f;
+            if (P.cp_on) cp_insert(B.cp_head, B.cp_next, P.cp_mask, P.cp_hinv, cp_ep, d, f);
         } else {
             const int r = prefix + lrank;  // global rank among removed ions, index order
             Rem rm;
@@ -455,7 +615,9 @@ __device__ __forceinline__ void push_scan_body(const Phys& P, const Bufs& B, int
         V[cap + d] = ivy;
         V[2 * cap + d] = ivz;
         B.id[dst][d] = iid;
-        B.fpos[d] = scaled(P, ix, iy, iz, ls_inv);
+        const float4 f = scaled(P, ix, iy, iz, ls_inv);
+        B.fpos[d] = f;
+        if (P.cp_on) cp_insert(B.cp_head, B.cp_next, P.cp_mask, P.cp_hinv, cp_ep, d, f);
         atomicAdd(&s_face[face], 1);
     }
     // slots vacated when fewer ions entered than left: far-away dummies for the pair kernel
@@ -473,6 +635,7 @@ __device__ __forceinline__ void push_scan_body(const Phys& P, const Bufs& B, int
         C->n_cur = n_new;
         C->tile_counter = 0u;
         C->done_counter = 0u;
+        C->cp_epoch = cp_ep;
     }
 }
 
@@ -515,55 +678,77 @@ __device__ __forceinline__ void kick_body(const Phys& P, const Bufs& B, const Fo
         z = X[2 * cap + i];
         float ax = 0.f, ay = 0.f, az = 0.f;
         if (!(P.flags & OD_F_NO_IONION)) {
-            // slots of this ion: the blocks that covered its tile (ordered-pair kernel), one
-            // per tile (symmetric kernel) or one per neighbour of the tile that holds its
-            // sorted position (cutoff: slots 0 .. degree - 1)
-            int ns = F.W;
-            int q = i;  // position in the pair kernel's ion order
-            if (F.sym && !F.cut) {
-                // symmetric: one slot per tile; tiles from the live count on hold only
-                // dummies and their slots are not written (exact zeros)
-                ns = min(ns, (C->n_cur + F.TI - 1) / F.TI);
-            } else if (F.cut) {
-                q = F.rank[i];
-                const int t = q / F.TI;
-                ns = F.nbr_start[t + 1] - F.nbr_start[t];
-            } else if (!F.sym) {
+            double px = 0.0, py = 0.0, pz = 0.0;  // pair sum in scaled units
+            if (F.sym) {
+                // symmetric kernels (all pairs or the cutoff's listed tile pairs): the
+                // fixed-point sum at the ion's position in the pair kernel's order, read and
+                // cleared for the next evaluation
+                const long long q = F.cut ? F.rank[i] : i;
+                long long* A = F.psum + q;
+                const long long qa = A[0], qb = A[F.psum_ld], qc = A[2 * F.psum_ld];
+                A[0] = 0;
+                A[F.psum_ld] = 0;
+                A[2 * F.psum_ld] = 0;
+                px = (double)qa * P.qinv;
+                py = (double)qb * P.qinv;
+                pz = (double)qc * P.qinv;
+            } else {
+                // ordered-pair kernel: the slots of the blocks that covered this ion's tile,
+                // summed in blocks of 16 (all loads of a block issued at once)
                 const int t = i / F.TI;
                 const long long u0 = (long long)t * F.JS;
-                ns = owner_of(u0 + F.JS - 1, F.U, F.G) - owner_of(u0, F.U, F.G) + 1;
-            }
-            // blocked sum over the slots (up to ~1000 with the symmetric kernel); whole
-            // blocks of 16 issue all their loads at once, the same order of additions
-            const float4* ps = B.part + q;
-            const long long ld = F.n_pad;
-            for (int s0 = 0; s0 < ns; s0 += 16) {
-                float bx = 0.f, by = 0.f, bz = 0.f;
-                if (s0 + 16 <= ns) {
-                    float4 p[16];
+                const int ns = (P.flags & OD_F_FP64_PAIRS) ? 1
+                                                            : owner_of(u0 + F.JS - 1, F.U, F.G) - owner_of(u0, F.U, F.G) + 1;
+                const float4* ps = B.part + i;
+                const long long ld = F.n_pad;
+                float sx = 0.f, sy = 0.f, sz = 0.f;
+                for (int s0 = 0; s0 < ns; s0 += 16) {
+                    float bx = 0.f, by = 0.f, bz = 0.f;
+                    if (s0 + 16 <= ns) {
+                        float4 p[16];
 #pragma unroll
-                    for (int s = 0; s < 16; ++s) p[s] = __ldcs(ps + (long long)(s0 + s) * ld);
+                        for (int s = 0; s < 16; ++s) p[s] = __ldcs(ps + (long long)(s0 + s) * ld);
 #pragma unroll
-                    for (int s = 0; s < 16; ++s) {
-                        bx += p[s].x;
-                        by += p[s].y;
-                        bz += p[s].z;
+                        for (int s = 0; s < 16; ++s) {
+                            bx += p[s].x;
+                            by += p[s].y;
+                            bz += p[s].z;
+                        }
+                    } else {
+                        for (int s = s0; s < ns; ++s) {
+                            const float4 p = __ldcs(ps + (long long)s * ld);
+                            bx += p.x;
+                            by += p.y;
+                            bz += p.z;
+                        }
                     }
-                } else {
-                    for (int s = s0; s < ns; ++s) {
-                        const float4 p = __ldcs(ps + (long long)s * ld);
-                        bx += p.x;
-                        by += p.y;
-                        bz += p.z;
-                    }
+                    sx += bx;
+                    sy += by;
+                    sz += bz;
                 }
-                ax += bx;
-                ay += by;
-                az += bz;
+                px = sx;
+                py = sy;
+                pz = sz;
             }
-            ax *= -P.k_ii;
-            ay *= -P.k_ii;
-            az *= -P.k_ii;
+            if (P.cp_on) {
+                const double* Xb = B.x[buf];
+                double cx, cy, cz;
+                close_pair_corr(B.cp_head, B.cp_next, B.fpos, P.cp_mask, P.cp_hinv, P.cp_dc2, C->cp_epoch, C->n_cur,
+                                P.ls_inv, i, x, y, z,
+                                [&](int j, double& xj, double& yj, double& zj) {
+                                    xj = Xb[j];
+                                    yj = Xb[cap + j];
+                                    zj = Xb[2 * cap + j];
+                                },
+                                cx, cy, cz);
+                px += cx;
+                py += cy;
+                pz += cz;
+            }
+            const double kk = -(double)P.k_ii;
+            ax = (float)(px * kk);
+            ay = (float)(py * kk);
+            az = (float)(pz * kk);
         }
         // bare Coulomb force of the grains (asymmetric model): FP32 terms from FP64
         // separations, like the pair forces
@@ -611,6 +796,16 @@ __device__ __forceinline__ void kick_body(const Phys& P, const Bufs& B, const Fo
             V[i] = vx;
             V[cap + i] = vy;
             V[2 * cap + i] = vz;
+        }
+    }
+    if (F.sym && !(P.flags & OD_F_NO_IONION)) {
+        // the accumulators after the live ions (far-away dummies and padding, whose mutual
+        // terms are not zero) are cleared too
+        const long long nthr = (long long)((P.N + BT - 1) / BT) * BT;
+        for (long long e = C->n_cur + (long long)i; e < F.n_pad; e += nthr) {
+            F.psum[e] = 0;
+            F.psum[F.psum_ld + e] = 0;
+            F.psum[2 * F.psum_ld + e] = 0;
         }
     }
     const unsigned bc = __ballot_sync(0xffffffffu, coll);

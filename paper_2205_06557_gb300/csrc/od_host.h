@@ -15,6 +15,7 @@ struct od_handle {
     od::Phys P{};
     od::Bufs B{};
     od::ForceArgs F{};
+    float qscale = 1.f;  // 2^K of the fixed-point pair sums
     int variant = 0;
     int upb = 8;  // pair-kernel work units per persistent block
     int bps = 0;  // persistent pair-kernel CTAs per SM (0 = occupancy limit)
@@ -80,12 +81,12 @@ double oml_charge(const od_params* p, double a);
 ForceArgs plan_forces(int N, int v, int sms, int units_per_block, int bps_cap);
 int default_variant(int N);
 int ensure_part(od_handle* h);
+void attach_sums(const od_handle* h, ForceArgs& F);
 int replan(od_handle* h, int N);
 int launch_pairs(od_handle* h, int after_push);
 int plan_n(const od_handle* h, long long n_live);
 int read_error_word(od_handle* h);
 int force_eval(od_handle* h);
-int cut_fit(od_handle* h);
 int ensure_series(od_handle* h, long long need);
 int ensure_io(od_handle* h);
 bool host_pinned(const void* p);
@@ -93,6 +94,7 @@ void free_cut(od_handle* h);
 void free_all(od_handle* h);
 int create_impl(const od_params* p, od_handle* h);
 int apply_force_config(od_handle* h, int variant, int upb, int bps);  // od_config.cu
+void set_close_pairs(od_handle* h);                                   // od_config.cu
 
 }  // namespace host
 }  // namespace od

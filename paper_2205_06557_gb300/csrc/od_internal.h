@@ -19,7 +19,7 @@ constexpr int ERR_NAN = 1;
 constexpr int ERR_TIMEOUT = 2;
 constexpr int ERR_OVERFLOW = 4;
 constexpr int ERR_PLACE = 8;
-constexpr int ERR_CUTCAP = 16;  // cutoff neighbour lists exceed the slot capacity
+constexpr int ERR_RANGE = 32;   // a pair partial sum beyond the fixed-point range (ions nearly coincide)
 constexpr long long SPIN_LIMIT = 1ll << 22;  // ~4 s of polling with the 1 us back-off
 constexpr int VTAB_K = 4096;                  // intervals of the tabulated inverse flux CDFs
 
@@ -50,6 +50,8 @@ struct Ctrl {
     double wsum[MAXD][REC];       // window sums of the records
     long long wcount;             // records in the window
     long long counters[OD_NCOUNT];
+    unsigned cp_epoch;            // close-pair cell lists: epoch of the last complete build (never 0)
+    unsigned cp_pad;
     double* series;               // [cap][MAXD][REC]
     int* evseries;                // [cap][EV]
     long long series_cap;
@@ -101,6 +103,15 @@ struct Phys {
     double gmax_b, gmax_t;  // flux integrals G(v_max) and G_top(v_min) the CDFs are normalised by
     long long spin_limit;  // polls before a device-side wait gives up (ERR_TIMEOUT)
     int test_hold_tile0;   // wait self-test: the first scan tile never publishes its prefix
+    // symmetric pair sums in fixed point: value x 2^K as int64 (qinv = 2^-K)
+    double qinv;
+    // close-pair correction of the FP32 position rounding: pairs closer than sqrt(cp_dc2)
+    // (scaled units) found through hashed cells of side 1 / cp_hinv
+    int cp_on;
+    unsigned cp_mask;  // buckets - 1 (a power of two)
+    float cp_hinv;
+    double cp_dc2;
+    double ls_inv;     // log2(e) / lambda_De in FP64
 };
 
 // Device buffers. Ion state is double-buffered (compaction writes the other copy).
@@ -110,7 +121,11 @@ struct Bufs {
     unsigned long long* id[2];
     float4* acc;   // accelerations of the current order
     float4* fpos;  // scaled positions for the pair kernel, padded with far-away dummies
-    float4* part;  // pair-kernel partial sums [W][n_pad]
+    float4* part;  // ordered pair-kernel partial sums [W][n_pad]
+    long long* psum;  // symmetric pair sums in fixed point [3][psum_ld] (zero between evaluations)
+    long long psum_ld;
+    unsigned long long* cp_head;  // close-pair cell buckets: (epoch << 32) | first ion
+    int* cp_next;                 // next ion of the same bucket, -1 at the end
     unsigned long long* tile_status;
     Inj* inj;
     Rem* rem;
@@ -126,16 +141,19 @@ struct ForceArgs {
     int JC;      // sources per chunk, multiple of BT
     int JS;      // chunks per tile
     int G;       // persistent blocks
-    int W;       // partial slots
+    int W;       // partial slots (ordered kernel; 0 for the symmetric kernels)
     long long U; // units = n_itiles * JS (symmetric: T (T + 1) / 2 tile pairs)
-    int sym;     // 1: symmetric kernel, JC = TI, JS = W = T tiles, every ion has T slots
+    int sym;     // 1: symmetric kernel, JC = TI, JS = T tiles; sums go to the fixed-point
+                 // accumulators psum (one int64 per ion and component, order-independent)
+    long long* psum;
+    long long psum_ld;
+    float qscale;  // 2^K: a partial sum v adds round(v 2^K)
+    int* err;      // the run's error word (ERR_RANGE)
     // ion-ion cutoff (symmetric tile pairs over z-sorted ions): switching zone in scaled
-    // units [cut_s0, cut_s0 + 1 / cut_inv_w]; ion i sits at rank[i] in the sorted order and
-    // its tile I has nbr_start[I + 1] - nbr_start[I] neighbours, whose sums fill its slots
-    // 0 .. degree - 1 (W = slot capacity)
+    // units [cut_s0, cut_s0 + 1 / cut_inv_w]; ion i sits at rank[i] in the sorted order,
+    // which is also its accumulator index
     int cut;
     float cut_s0, cut_inv_w;
-    const int* nbr_start;
     const int* rank;
     // dynamic unit queue of the packed symmetric and cutoff kernels: [0] next unit,
     // [1] CTAs finished (both zero between launches)
@@ -175,6 +193,7 @@ int launch_pad(const Phys& P, const Bufs& B, cudaStream_t s);
 int launch_push_scan(const Phys& P, const Bufs& B, cudaStream_t s);
 int launch_forces(const Phys& P, const Bufs& B, const ForceArgs& F, int variant, cudaStream_t s);
 int launch_kick(const Phys& P, const Bufs& B, const ForceArgs& F, int mode, cudaStream_t s);
+int launch_cp_bump(const Bufs& B, cudaStream_t s);  // advance the close-pair list epoch
 int launch_forces_f64(const Phys& P, const Bufs& B, int after_push, cudaStream_t s);
 int launch_dust(const Phys& P, const Bufs& B, int mode, cudaStream_t s);
 int launch_stats(const Phys& P, const Bufs& B, double* mean_se, cudaStream_t s);
@@ -200,20 +219,12 @@ struct CutBufs {
     float4* fsort; // sorted scaled positions, far dummies after N
     float4* box_lo;
     float4* box_hi;
-    int* nbr_start;  // [T + 1]
-    int* nbr;        // [T * T] neighbour tiles, ascending per tile
-    int4* units;     // [T (T + 1) / 2] (I, J >= I, slot of J in I's list, slot of I in J's list)
+    int2* units;     // [T (T + 1) / 2] tile pairs (I, J >= I | plain flag) whose boxes meet
     int* n_units;
-    int* cnt;        // [T] neighbours per tile
     int* ucnt;       // [T] tile pairs (J >= I) per tile
     int* ustart;     // [T] first unit of each tile
-    int* over;       // [0] 1: the lists exceed max_deg; [1] largest tile degree of the last lists
-    int max_deg;     // slot capacity per ion
-    int* err;        // the run's error word (Ctrl::err)
 };
-// lists_only: sort, boxes, degrees and the overflow check, no pair evaluation
-int launch_forces_cut(const Phys& P, const Bufs& B, const ForceArgs& F, const CutBufs& C, int grid, cudaStream_t s,
-                      int lists_only = 0);
+int launch_forces_cut(const Phys& P, const Bufs& B, const ForceArgs& F, const CutBufs& C, int grid, cudaStream_t s);
 int launch_cut_dummies(const CutBufs& C, int N, int n_pad, cudaStream_t s);
 int cut_blocks_per_sm(int ipt);
 

@@ -107,7 +107,7 @@ struct CkptHeader {
     uint64_t ctrl_bytes;
     double r_cut, r_switch;  // ion-ion cutoff (0: none)
 };
-static const char kCkptMagic[8] = {'O', 'D', 'C', 'K', 'P', 'T', '0', '1'};
+static const char kCkptMagic[8] = {'O', 'D', 'C', 'K', 'P', 'T', '0', '2'};
 
 int od_save(od_handle* h, const char* path)
 {
@@ -260,8 +260,6 @@ int od_load(const char* path, void* cuda_stream, od_handle** out)
         if ((rc = replan(h, plan_n(h, N)))) return done(rc);
         if (launch_fpos(h->P, h->B, buf, h->stream)) return done(fail(h, OD_ECUDA, "position refresh failed"));
     }
-    // slot capacity for the saved positions (the saved accelerations stay)
-    if ((rc = cut_fit(h))) return done(rc);
     h->graph_ok = false;
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return done(fail(h, OD_ECUDA, "checkpoint upload failed"));
     return done(read_error_word(h));

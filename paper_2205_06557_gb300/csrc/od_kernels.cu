@@ -65,7 +65,11 @@ __global__ void k_init_ions(Phys P, Bufs B, double ls_inv)
     B.fpos[i] = scaled(P, x, y, z, ls_inv);
 }
 
-// scaled positions for the pair kernel from state buffer `buf`; dummies beyond N
+// publishes the close-pair lists built by k_fpos (their epoch becomes the current one)
+__global__ void k_cp_bump(Ctrl* C) { C->cp_epoch = cp_next_epoch(C->cp_epoch); }
+
+// scaled positions for the pair kernel from state buffer `buf` (entered into the
+// close-pair cell lists); dummies beyond N
 __global__ void k_fpos(Phys P, Bufs B, int buf, double ls_inv)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -73,7 +77,9 @@ __global__ void k_fpos(Phys P, Bufs B, int buf, double ls_inv)
     const int n = B.ctrl->n_cur;  // ions alive
     if (i < n) {
         const double* X = B.x[buf];
-        B.fpos[i] = scaled(P, X[i], X[B.cap + i], X[2 * B.cap + i], ls_inv);
+        const float4 f = scaled(P, X[i], X[B.cap + i], X[2 * B.cap + i], ls_inv);
+        B.fpos[i] = f;
+        if (P.cp_on) cp_insert(B.cp_head, B.cp_next, P.cp_mask, P.cp_hinv, cp_next_epoch(B.ctrl->cp_epoch), i, f);
     } else {
         // far-away dummies: 2^-s underflows to zero, so they add nothing
         const float far = 3.0e4f + 7.0f * (float)(i - n);
@@ -124,49 +130,47 @@ __global__ void k_stats(Phys P, Bufs B, double* out)
 }
 
 // ------------------------------------------------ App. A cavity-potential grid
-// I(r, z) = int_cyl exp(-|r - r'|/lambda) / |r - r'| d^3r' at each grid node, written in
-// spherical coordinates about the node: the radial integral is lambda^2 (1 - (1 + x) e^-x)
-// with x = S / lambda, S the distance to the boundary along the ray; the angles use
-// Gauss-Legendre on the pieces where S is smooth (rims split the polar angle).
+// I(r0, z0) = int_cyl exp(-|r - r'|/lambda) / |r - r'| d^3r' at each grid node, by slices
+// of the cylinder at height z' = z0 + t: in the plane of a slice, polar coordinates about
+// the node's projection give the in-plane radial integral in closed form,
+//   int_0^S s exp(-sqrt(s^2 + t^2)/lambda) / sqrt(s^2 + t^2) ds
+//       = lambda (exp(-|t|/lambda) - exp(-sqrt(S^2 + t^2)/lambda)),
+// S(psi) = -r0 cos psi + sqrt(R^2 - r0^2 sin^2 psi) the distance to the slice's rim in
+// direction psi.  The first term integrates in closed form over psi and t:
+// 2 pi lambda^2 (2 - exp(-a/lambda) - exp(-b/lambda)), a and b the distances from the
+// node to the end faces.  The second is smooth in psi (twice the integral over [0, pi])
+// and in t on each side of the node (t in [0, a] and [0, b]); both go to Gauss-Legendre.
+// On the rim (r0 = R) S vanishes for psi < pi/2, where that part is exp(-|t|/lambda)
+// again and integrates in closed form.
 __global__ void k_eout_grid(double R, double H, double lam, int nx, int nz, int nq, const double* __restrict__ glx,
                             const double* __restrict__ glw, double* __restrict__ out)
 {
     __shared__ double s_part[128];
     const int node = blockIdx.x;
     const int kr = node / (nz + 1), kz = node % (nz + 1);
-    const double r0 = R * kr / nx, hz = 0.5 * H, z0 = hz * kz / nz;
+    const double r0 = R * kr / nx, z0 = 0.5 * H * kz / nz;
+    const double a = 0.5 * H - z0, b = 0.5 * H + z0;
     const double PI = 3.141592653589793;
+    const bool rim = kr == nx;
+    const double p0 = rim ? 0.5 * PI : 0.0, p1 = PI;  // the psi range with S > 0
     double acc = 0.0;
-    for (int ip = threadIdx.x; ip < 2 * nq; ip += blockDim.x) {
-        const int seg = ip / nq, q = ip % nq;
-        const double pa = seg * 0.5 * PI;
-        const double phi = pa + 0.25 * PI * (1.0 + glx[q]);
-        const double wphi = 0.25 * PI * glw[q];
-        double sphi, cphi;
-        sincos(phi, &sphi, &cphi);
-        const double disc = R * R - r0 * r0 * sphi * sphi;
-        double sh = -r0 * cphi + sqrt(fmax(disc, 0.0));
-        sh = fmax(sh, 0.0);
-        const double e1 = atan2(sh, hz - z0), e2 = PI - atan2(sh, hz + z0);
-        const double edges[4] = {0.0, e1, e2, PI};
-        double inner = 0.0;
-        for (int s3 = 0; s3 < 3; ++s3) {
-            const double ta = edges[s3], tb = edges[s3 + 1];
-            if (!(tb > ta)) continue;
-            for (int it = 0; it < nq; ++it) {
-                const double th = 0.5 * (ta + tb) + 0.5 * (tb - ta) * glx[it];
-                const double wth = 0.5 * (tb - ta) * glw[it];
-                double sth, cth;
-                sincos(th, &sth, &cth);
-                const double S = s3 == 0 ? (hz - z0) / cth : (s3 == 1 ? sh / sth : (hz + z0) / (-cth));
-                const double xs = S / lam;
-                double f;
-                if (xs < 1e-3) f = xs * xs * (0.5 + xs * (-1.0 / 3.0 + xs * (0.125 + xs * (-1.0 / 30.0))));
-                else f = -expm1(-xs) - xs * exp(-xs);
-                inner += wth * f * sth;
-            }
+    // one (psi node, side of the node) pair per thread
+    for (int w = threadIdx.x; w < 2 * nq; w += blockDim.x) {
+        const int iq = w >> 1, side = w & 1;
+        const double L = side == 0 ? a : b;
+        if (!(L > 0.0)) continue;
+        const double psi = 0.5 * (p0 + p1) + 0.5 * (p1 - p0) * glx[iq];
+        const double wpsi = 0.5 * (p1 - p0) * glw[iq];
+        double sp, cp;
+        sincos(psi, &sp, &cp);
+        const double S = rim ? -2.0 * R * cp : -r0 * cp + sqrt(fmax(R * R - r0 * r0 * sp * sp, 0.0));
+        const double S2 = S * S;
+        double sum = 0.0;
+        for (int it = 0; it < nq; ++it) {
+            const double t = 0.5 * L * (1.0 + glx[it]);
+            sum += glw[it] * exp(-sqrt(S2 + t * t) / lam);
         }
-        acc += wphi * inner;
+        acc += wpsi * 0.5 * L * sum;
     }
     s_part[threadIdx.x] = acc;
     __syncthreads();
@@ -174,7 +178,13 @@ __global__ void k_eout_grid(double R, double H, double lam, int nx, int nz, int 
         if ((int)threadIdx.x < w) s_part[threadIdx.x] += s_part[threadIdx.x + w];
         __syncthreads();
     }
-    if (threadIdx.x == 0) out[node] = 2.0 * lam * lam * s_part[0];
+    if (threadIdx.x == 0) {
+        const double ea = exp(-a / lam), eb = exp(-b / lam);
+        double I = 2.0 * PI * lam * lam * (2.0 - ea - eb) - 2.0 * lam * s_part[0];
+        // rim: psi in [0, pi/2] (S = 0), both signs of psi
+        if (rim) I -= 2.0 * (0.5 * PI) * lam * lam * ((1.0 - ea) + (1.0 - eb));
+        out[node] = I;
+    }
 }
 
 // ---------------------------------------------------------------- launchers
@@ -194,11 +204,18 @@ int launch_init_ions(const Phys& P, const Bufs& B, cudaStream_t s)
     return ck(cudaGetLastError());
 }
 
+int launch_cp_bump(const Bufs& B, cudaStream_t s)
+{
+    k_cp_bump<<<1, 1, 0, s>>>(B.ctrl);
+    return ck(cudaGetLastError());
+}
+
 int launch_fpos(const Phys& P, const Bufs& B, int buf, cudaStream_t s)
 {
     if (P.n_pad == 0) return 0;
     const double ls_inv = 1.4426950408889634 * P.lam_inv;
     k_fpos<<<(P.n_pad + 255) / 256, 256, 0, s>>>(P, B, buf, ls_inv);
+    if (P.cp_on) k_cp_bump<<<1, 1, 0, s>>>(B.ctrl);
     return ck(cudaGetLastError());
 }
 
@@ -320,17 +337,17 @@ int launch_forces(const Phys& P, const Bufs& B, const ForceArgs& F, int v, cudaS
     }
     OD_FORCE_VARIANTS(OD_V)
 #undef OD_V
-#define OD_V(bt, ipt)                                                \
-    if (v == idx++) {                                                \
-        k_forces_sym<bt, ipt><<<F.G, bt, 0, s>>>(B.fpos, B.part, F); \
-        return ck(cudaGetLastError());                               \
+#define OD_V(bt, ipt)                                        \
+    if (v == idx++) {                                        \
+        k_forces_sym<bt, ipt><<<F.G, bt, 0, s>>>(B.fpos, F); \
+        return ck(cudaGetLastError());                       \
     }
     OD_SYM_VARIANTS(OD_V)
 #undef OD_V
-#define OD_V(bt, ipt)                                                 \
-    if (v == idx++) {                                                 \
-        k_forces_sym2<bt, ipt><<<F.G, bt, 0, s>>>(B.fpos, B.part, F); \
-        return ck(cudaGetLastError());                                \
+#define OD_V(bt, ipt)                                         \
+    if (v == idx++) {                                         \
+        k_forces_sym2<bt, ipt><<<F.G, bt, 0, s>>>(B.fpos, F); \
+        return ck(cudaGetLastError());                        \
     }
     OD_SYM2_VARIANTS(OD_V)
 #undef OD_V
@@ -465,36 +482,79 @@ int launch_eout_grid(double R, double H, double lam, int nx, int nz, int nq, con
 
 // ---------------------------------------------- no-allocation pair forces
 // A variant of the pair-force computation for callers that cannot allocate device
-// memory.  Its scratch (scaled positions and the per-chunk partial sums) lives in
-// one file-scope device array of fixed size that every GPU loading this library
-// holds until the process exits.  Host code only sees a stand-in for the array's
-// name, so the device address is looked up once per device with
-// cudaGetSymbolAddress and passed to the kernels.
+// memory.  Its scratch (scaled positions, the per-chunk partial sums, the close-pair
+// cell buckets and links and one bound word) lives in one file-scope device array of
+// fixed size that every GPU loading this library holds until the process exits.  Host
+// code only sees a stand-in for the array's name, so the device address is looked up
+// with cudaGetSymbolAddress (once per device and context) and passed to the kernels.
 namespace od {
 namespace {
 constexpr int kStaticBT = 128, kStaticIPT = 2, kStaticTI = kStaticBT * kStaticIPT;
-constexpr int kStaticSlots = 8;  // source chunks per target tile
-constexpr long long kStaticFloat4 = (long long)OD_STATIC_MAX_IONS * (1 + kStaticSlots);
+constexpr int kStaticSlots = 8;                       // source chunks per target tile
+constexpr int kStaticBuckets = 2 * OD_STATIC_MAX_IONS; // close-pair cell buckets (u64 each)
+// layout in float4 units: positions, partial slots, buckets, links, bound word
+constexpr long long kOffPart = OD_STATIC_MAX_IONS;
+constexpr long long kOffHead = kOffPart + (long long)OD_STATIC_MAX_IONS * kStaticSlots;
+constexpr long long kOffNext = kOffHead + kStaticBuckets / 2;
+constexpr long long kOffBound = kOffNext + OD_STATIC_MAX_IONS / 4;
+constexpr long long kStaticFloat4 = kOffBound + 1;
 static_assert(OD_STATIC_MAX_IONS % kStaticTI == 0, "capacity must be a whole number of tiles");
+static_assert((kStaticBuckets & (kStaticBuckets - 1)) == 0, "bucket count must be a power of two");
 }  // namespace
 
 static __device__ __align__(256) float4 g_static_scratch[kStaticFloat4];
 
-__global__ void k_static_scale(const double* __restrict__ x, int n, int n_pad, double ls_inv, float4* __restrict__ fpos)
+// correction distance and cell width (scaled units) from the largest |s|: pairs closer
+// than 0.005 max(1, |s|max) get their FP64 value
+__device__ __forceinline__ void static_cp_params(const unsigned* bound, double& dc2, float& hinv)
+{
+    const double smax = (double)__uint_as_float(*bound);
+    const double dc = 0.005 * fmax(1.0, smax);
+    dc2 = dc * dc;
+    hinv = (float)(1.0 / (1.05 * dc));
+}
+
+// largest |coordinate| in scaled units (non-negative floats order like their bits)
+__global__ void k_static_bound(const double* __restrict__ x, int n, double ls_inv, unsigned* __restrict__ bound)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    float m = 0.f;
+    if (i < n)
+        m = fmaxf(fabsf((float)(x[3 * i] * ls_inv)), fmaxf(fabsf((float)(x[3 * i + 1] * ls_inv)),
+                                                         fabsf((float)(x[3 * i + 2] * ls_inv))));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(bound, __float_as_uint(m));
+}
+
+// scaled FP32 positions, entered into the close-pair cells; padding beyond n goes
+// 256 scaled units (a factor 2^-256 in the pair term: exactly zero in FP32) past the
+// largest coordinate and 256 apart
+__global__ void k_static_scale(const double* __restrict__ x, int n, int n_pad, double ls_inv, float4* __restrict__ fpos,
+                               unsigned long long* __restrict__ head, int* __restrict__ next,
+                               const unsigned* __restrict__ bound, unsigned epoch)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_pad) return;
     if (i < n) {
-        fpos[i] = make_float4((float)(x[3 * i] * ls_inv), (float)(x[3 * i + 1] * ls_inv), (float)(x[3 * i + 2] * ls_inv),
-                              0.0f);
+        const float4 f = make_float4((float)(x[3 * i] * ls_inv), (float)(x[3 * i + 1] * ls_inv),
+                                     (float)(x[3 * i + 2] * ls_inv), 0.0f);
+        fpos[i] = f;
+        double dc2;
+        float hinv;
+        static_cp_params(bound, dc2, hinv);
+        cp_insert(head, next, (unsigned)kStaticBuckets - 1u, hinv, epoch, i, f);
     } else {
-        const float far = 3.0e4f + 7.0f * (float)(i - n);
+        const float far = __uint_as_float(*bound) + 256.0f * (float)(i - n + 1);
         fpos[i] = make_float4(far, far, far, 0.0f);
     }
 }
 
-__global__ void k_static_reduce(const float4* __restrict__ part, int n, int n_pad, int slots, float kscale,
-                                float* __restrict__ a)
+// sum of each ion's partial slots, plus the close-pair correction, times -k
+__global__ void k_static_reduce(const float4* __restrict__ part, const double* __restrict__ x, int n, int n_pad,
+                                int slots, double ls_inv, double kscale, const float4* __restrict__ fpos,
+                                const unsigned long long* __restrict__ head, const int* __restrict__ next,
+                                const unsigned* __restrict__ bound, unsigned epoch, float* __restrict__ a)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -505,22 +565,55 @@ __global__ void k_static_reduce(const float4* __restrict__ part, int n, int n_pa
         ay += p.y;
         az += p.z;
     }
-    a[3 * i] = -kscale * ax;
-    a[3 * i + 1] = -kscale * ay;
-    a[3 * i + 2] = -kscale * az;
+    double dc2;
+    float hinv;
+    static_cp_params(bound, dc2, hinv);
+    double cx, cy, cz;
+    close_pair_corr(head, next, fpos, (unsigned)kStaticBuckets - 1u, hinv, dc2, epoch, n, ls_inv, i, x[3 * i],
+                    x[3 * i + 1], x[3 * i + 2],
+                    [&](int j, double& xj, double& yj, double& zj) {
+                        xj = x[3 * j];
+                        yj = x[3 * j + 1];
+                        zj = x[3 * j + 2];
+                    },
+                    cx, cy, cz);
+    a[3 * i] = (float)(-kscale * ((double)ax + cx));
+    a[3 * i + 1] = (float)(-kscale * ((double)ay + cy));
+    a[3 * i + 2] = (float)(-kscale * ((double)az + cz));
 }
 
-static float4* static_scratch_address(int dev, int* rc)
+// The array's device address in the current context of device dev, and a fresh epoch
+// for the close-pair buckets (each call's lists get their own tag).  The address is
+// looked up again when the device's context changes (e.g. after cudaDeviceReset, which
+// reloads the module): the context is identified through the driver entry point
+// cuCtxGetCurrent, fetched from the runtime so that the library needs no link to libcuda.
+static float4* static_scratch_address(int dev, int* rc, unsigned* epoch)
 {
     static std::mutex mu;
     static float4* addr[256] = {nullptr};
+    static void* ctx_of[256] = {nullptr};
+    static unsigned ep[256] = {0};
     *rc = OD_OK;
     if (dev < 0 || dev >= 256) {
         *rc = OD_EINVAL;
         return nullptr;
     }
     std::lock_guard<std::mutex> lock(mu);
-    if (!addr[dev]) {
+    typedef int (*CtxGetCurrent)(void**);
+    static CtxGetCurrent get_ctx = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        looked = true;
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_ctx = (CtxGetCurrent)fn;
+        cudaGetLastError();
+    }
+    void* ctx = nullptr;
+    if (get_ctx) get_ctx(&ctx);
+    if (!addr[dev] || ctx != ctx_of[dev]) {
         void* p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
         if (e != cudaSuccess || !p) {
@@ -529,7 +622,11 @@ static float4* static_scratch_address(int dev, int* rc)
             return nullptr;
         }
         addr[dev] = (float4*)p;
+        ctx_of[dev] = ctx;
+        ep[dev] = 0;  // a new context starts from a zeroed array
     }
+    ep[dev] = ep[dev] + 1u == 0u ? 1u : ep[dev] + 1u;
+    *epoch = ep[dev];
     return addr[dev];
 }
 
@@ -552,7 +649,8 @@ extern "C" int od_pair_accel_static(const double* x, int64_t n, double lambda_De
         return OD_ENODEV;
     }
     int rc = OD_OK;
-    float4* base = static_scratch_address(dev, &rc);
+    unsigned epoch = 0;
+    float4* base = static_scratch_address(dev, &rc, &epoch);
     if (!base) return rc;
     if (n == 0) return OD_OK;
     cudaStream_t s = (cudaStream_t)stream;
@@ -568,16 +666,24 @@ extern "C" int od_pair_accel_static(const double* x, int64_t n, double lambda_De
     F.G = (int)F.U;  // one unit per block: the partial slot of a block is its chunk index
     F.W = F.JS;
     float4* fpos = base;
-    float4* part = base + OD_STATIC_MAX_IONS;
-    k_static_scale<<<(F.n_pad + 255) / 256, 256, 0, s>>>(x, (int)n, F.n_pad, ls_inv, fpos);
-    k_forces<kStaticBT, kStaticIPT><<<F.G, kStaticBT, 0, s>>>(fpos, part, F);
-    const float kscale = (float)(k * ls_inv * ls_inv);
-    k_static_reduce<<<(int)((n + 255) / 256), 256, 0, s>>>(part, (int)n, F.n_pad, F.JS, kscale, a);
-    const cudaError_t e = cudaGetLastError();
+    float4* part = base + kOffPart;
+    unsigned long long* head = (unsigned long long*)(base + kOffHead);
+    int* next = (int*)(base + kOffNext);
+    unsigned* bound = (unsigned*)(base + kOffBound);
+    // the bound word is the one value that must start at zero on every call
+    cudaError_t e = cudaMemsetAsync(bound, 0, sizeof(unsigned), s);
+    if (e == cudaSuccess) {
+        k_static_bound<<<(int)((n + 255) / 256), 256, 0, s>>>(x, (int)n, ls_inv, bound);
+        k_static_scale<<<(F.n_pad + 255) / 256, 256, 0, s>>>(x, (int)n, F.n_pad, ls_inv, fpos, head, next, bound, epoch);
+        k_forces<kStaticBT, kStaticIPT><<<F.G, kStaticBT, 0, s>>>(fpos, part, F);
+        const double kscale = k * ls_inv * ls_inv;
+        k_static_reduce<<<(int)((n + 255) / 256), 256, 0, s>>>(part, x, (int)n, F.n_pad, F.JS, ls_inv, kscale, fpos,
+                                                               head, next, bound, epoch, a);
+        e = cudaGetLastError();
+    }
     if (e != cudaSuccess) {
         set_global_error(std::string("od_pair_accel_static: launch failed: ") + cudaGetErrorString(e));
         return OD_ECUDA;
     }
     return OD_OK;
 }
-

@@ -161,13 +161,11 @@ __device__ __forceinline__ void tri_unit(long long u, int T, int& I, int& J)
 // (double buffered, one barrier per SUB sources).
 // Unit (I, I): the ordered pairs of the tile through pair_chunk (the self pair is 0).
 //
-// Partial slots (deterministic, each written exactly once per evaluation): the target-
-// side sum of unit (I, J) goes to slot J of the ions of tile I, its source-side sum to
-// slot I of the ions of tile J, and unit (I, I) fills slot I of tile I.  Every ion has
-// T slots, summed by the kick.
+// Sums: the unit's FP32 target-side sums (ions of tile I) and source-side sums (ions of
+// tile J) are added to the ions' fixed-point accumulators (fixed_add3), so the result
+// does not depend on the order in which units finish; the kick reads and clears them.
 template <int BT, int IPT>
-__global__ void __launch_bounds__(BT) k_forces_sym(const float4* __restrict__ fpos, float4* __restrict__ part,
-                                                   ForceArgs F)
+__global__ void __launch_bounds__(BT) k_forces_sym(const float4* __restrict__ fpos, ForceArgs F)
 {
     constexpr int NW = BT / 32;
     constexpr int TI = BT * IPT;
@@ -240,13 +238,13 @@ __global__ void __launch_bounds__(BT) k_forces_sym(const float4* __restrict__ fp
                         sy += s_acc[buf][1][ww][j];
                         sz += s_acc[buf][2][ww][j];
                     }
-                    part[(long long)I * F.n_pad + jb + sc * SUB + j] = make_float4(sx, sy, sz, 0.f);
+                    fixed_add3(F.psum, F.psum_ld, jb + sc * SUB + j, sx, sy, sz, F.qscale, F.err);
                 }
             }
         }
-        float4* out = part + (long long)J * F.n_pad + I * TI + threadIdx.x;
 #pragma unroll
-        for (int k = 0; k < IPT; ++k) out[k * BT] = make_float4(ax[k], ay[k], az[k], 0.f);
+        for (int k = 0; k < IPT; ++k)
+            fixed_add3(F.psum, F.psum_ld, I * TI + k * BT + threadIdx.x, ax[k], ay[k], az[k], F.qscale, F.err);
         if (++J == T) J = ++I;
     }
 }
@@ -347,20 +345,16 @@ __device__ __forceinline__ f32x2 pair_c3x2_cut(f32x2 dx, f32x2 dy, f32x2 dz, flo
 constexpr int SYM_SUB = 128;  // sources per combine step of the symmetric kernels
 
 // One tile-pair unit (I, J >= I) of the symmetric kernel with packed FP32 pairs: the same
-// units, slots and fixed combine order as k_forces_sym, but the travelling packet holds
+// units, fixed-point sums and fixed combine order as k_forces_sym, but the travelling packet holds
 // two sources (the lane's sources q*64 + lane and q*64 + 32 + lane of the group), each
 // target is duplicated into both halves of a pair, and every FP32 operation of the pair
 // term acts on the two sources in one instruction.  Source-side sums are accumulated
 // with the target-side sign and negated when the warps' sums are combined.  Every unit
 // starts on combine buffer 0 and ends on buffer 1, so consecutive units need no barrier
 // between them beyond the one per combine step.
-// slot_i / slot_j: the partial slots that receive the sums of the ions of tile I / J (the
-// all-pairs kernels pass J / I; the cutoff passes the positions of J and I in the other
-// tile's neighbour list)
 template <int BT, int IPT, bool CUT = false>
-__device__ __forceinline__ void sym2_unit(const float4* __restrict__ fpos, float4* __restrict__ part,
-                                          const ForceArgs& F, int I, int J, float (&s_acc)[2][3][BT / 32][SYM_SUB],
-                                          float4* sj, int slot_i, int slot_j)
+__device__ __forceinline__ void sym2_unit(const float4* __restrict__ fpos, const ForceArgs& F, int I, int J,
+                                          float (&s_acc)[2][3][BT / 32][SYM_SUB], float4* sj)
 {
     constexpr int NW = BT / 32;
     constexpr int TI = BT * IPT;
@@ -440,7 +434,7 @@ __device__ __forceinline__ void sym2_unit(const float4* __restrict__ fpos, float
                     sy += s_acc[buf][1][ww][j];
                     sz += s_acc[buf][2][ww][j];
                 }
-                part[(long long)slot_j * F.n_pad + jb + sc * SYM_SUB + j] = make_float4(-sx, -sy, -sz, 0.f);
+                fixed_add3(F.psum, F.psum_ld, jb + sc * SYM_SUB + j, -sx, -sy, -sz, F.qscale, F.err);
             }
         }
 #pragma unroll
@@ -454,13 +448,14 @@ __device__ __forceinline__ void sym2_unit(const float4* __restrict__ fpos, float
             az[k] = l0 + h0;
         }
     }
-    float4* out = part + (long long)slot_i * F.n_pad + I * TI + threadIdx.x;
 #pragma unroll
-    for (int k = 0; k < IPT; ++k) out[k * BT] = make_float4(ax[k], ay[k], az[k], 0.f);
+    for (int k = 0; k < IPT; ++k)
+        fixed_add3(F.psum, F.psum_ld, I * TI + k * BT + threadIdx.x, ax[k], ay[k], az[k], F.qscale, F.err);
 }
 
-// Dynamic unit queue: a persistent CTA takes the next unit index from sched[0] (units
-// write fixed slots, so which CTA evaluates a unit changes no result); the last CTA to
+// Dynamic unit queue: a persistent CTA takes the next unit index from sched[0] (the
+// fixed-point sums are order-independent, so which CTA evaluates a unit changes no
+// result); the last CTA to
 // finish resets both words for the next launch on the stream.
 __device__ __forceinline__ long long next_unit(unsigned long long* sched, long long& s_u)
 {
@@ -482,16 +477,15 @@ __device__ __forceinline__ void leave_queue(unsigned long long* sched)
 // queue.  The 8-target variants are held to 128 registers (a few spills) for one more
 // resident CTA per SM, which measured 1% faster than their natural 133.
 template <int BT, int IPT>
-__global__ void __launch_bounds__(BT, (IPT == 8 ? 65536 / (BT * 128) : 1)) k_forces_sym2(const float4* __restrict__ fpos, float4* __restrict__ part,
-                                                    ForceArgs F)
+__global__ void __launch_bounds__(BT, (IPT == 8 ? 65536 / (BT * 128) : 1))
+    k_forces_sym2(const float4* __restrict__ fpos, ForceArgs F)
 {
     constexpr int TI = BT * IPT;
     __shared__ float s_acc[2][3][BT / 32][SYM_SUB];
     __shared__ float4 sj[BT];
     __shared__ long long s_u;
-    // tiles from the live count on hold only far-away dummies, whose terms are exactly
-    // zero: units that reach such a tile (J >= I) are skipped, and the kick reads only the
-    // slots of the live tiles.  The count is read again for every unit (a volatile load),
+    // tiles from the live count on hold only far-away dummies, whose terms with live ions
+    // are exactly zero: units that reach such a tile (J >= I) are skipped.  The count is read again for every unit (a volatile load),
     // so that it takes no register across the unit's code, which sits at the register cap.
     for (;;) {
         const long long u = next_unit(F.sched, s_u);
@@ -499,7 +493,7 @@ __global__ void __launch_bounds__(BT, (IPT == 8 ? 65536 / (BT * 128) : 1)) k_for
         int I, J;
         tri_unit(u, F.JS, I, J);
         if (F.n_live && J * TI >= *(volatile const int*)F.n_live) continue;
-        sym2_unit<BT, IPT>(fpos, part, F, I, J, s_acc, sj, J, I);
+        sym2_unit<BT, IPT>(fpos, F, I, J, s_acc, sj);
     }
     leave_queue(F.sched);
 }
