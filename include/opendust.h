@@ -344,7 +344,7 @@ const char* od_last_error(const od_handle* h);
  * Computes the ion-ion Yukawa accelerations of n ions already in device memory,
  *     a_i = k * sum_{j != i} (1 + r_ij/lambda_De) exp(-r_ij/lambda_De) (x_i - x_j) / r_ij^3,
  * with the same FP32 pair arithmetic as od_step and the same FP64 correction of pairs
- * closer than 0.005 max(1, |s|max) scaled units s = r log2(e) / lambda_De (k = q^2 /
+ * closer than 0.005 max(1, |s|max / 4) scaled units s = r log2(e) / lambda_De (k = q^2 /
  * (4 pi eps0 m) for superions of charge q and mass m).
  *   x       device, [n][3] FP64 positions (m), read only
  *   n       0 .. OD_STATIC_MAX_IONS (OD_EINVAL beyond)

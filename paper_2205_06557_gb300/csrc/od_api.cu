@@ -386,12 +386,13 @@ void derive(const od_params* p, Phys& P, od_handle* h)
     const int K = (int)std::max(-100.0, std::min(100.0, std::floor(30.0 - std::log2(std::max(ts, 1e-300)))));
     P.qinv = std::ldexp(1.0, -K);
     h->qscale = (float)std::ldexp(1.0, K);
-    // close-pair correction: pairs nearer than 0.005 max(1, |s|max) scaled units (the FP32
-    // rounding of |s| moves them most relative to their separation); hashed cells 5% wider
+    // close-pair correction: pairs nearer than d_c = 0.005 max(1, |s|max / 4) scaled units
+    // (the FP32 rounding of |s| moves them most relative to their separation; what it
+    // leaves in the farther pairs grows like |s|max / d_c); hashed cells 2.1 d_c wide
     const double smax = std::sqrt(Rs * Rs + Hs * Hs);
-    const double dc = 0.005 * std::max(1.0, smax);
+    const double dc = 0.005 * std::max(1.0, 0.25 * smax);
     P.cp_dc2 = dc * dc;
-    P.cp_hinv = (float)(1.0 / (1.05 * dc));
+    P.cp_hinv = (float)(1.0 / (2.1 * dc));
     P.cp_on = !(p->flags & (OD_F_NO_IONION | OD_F_FP64_PAIRS));
     double* o = h->info;
     o[0] = lam;
@@ -817,9 +818,24 @@ int create_impl(const od_params* p, od_handle* h)
     c0.next_id = (unsigned long long)N;
     c0.n_cur = N;
     c0.cp_epoch = 1;  // bucket words start at epoch 0, which no build uses
-    for (int k = 0; k < p->n_dust; ++k)
-        c0.Q[k] = p->charge_model == OD_Q_OML ? oml_charge(p, p->dust[k].radius) : p->dust[k].q0;
+    for (int k = 0; k < p->n_dust; ++k) c0.Q[k] = p->charge_model == OD_Q_OML ? 0.0 : p->dust[k].q0;
     OD_CK(h, cudaMemcpyAsync(B.ctrl, &c0, sizeof(Ctrl), cudaMemcpyHostToDevice, h->stream));
+    if (p->charge_model == OD_Q_OML && p->n_dust > 0) {
+        // the grains' OML floating charges, solved on the device
+        std::vector<double> gx, gw;
+        gl_nodes(96, gx, gw);
+        double* d_gl = nullptr;
+        OD_CK(h, cudaMalloc(&d_gl, sizeof(double) * 2 * gx.size()));
+        OD_CK(h, cudaMemcpyAsync(d_gl, gx.data(), sizeof(double) * gx.size(), cudaMemcpyHostToDevice, h->stream));
+        OD_CK(h, cudaMemcpyAsync(d_gl + gx.size(), gw.data(), sizeof(double) * gw.size(), cudaMemcpyHostToDevice,
+                                 h->stream));
+        const int lrc = launch_oml_charge(h->P, B, p->n_inf, p->ion_mass, p->ion_charge_number, p->T_e, (int)gx.size(),
+                                          d_gl, d_gl + gx.size(), h->stream);
+        const cudaError_t se = cudaStreamSynchronize(h->stream);
+        cudaFree(d_gl);
+        if (lrc) return cuda_fail(h, (cudaError_t)lrc, "launch_oml_charge");
+        OD_CK(h, se);
+    }
     int rc = replan(h, n_plan);
     if (rc) return rc;
     Phys Pi = h->P;

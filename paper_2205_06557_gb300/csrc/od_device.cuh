@@ -188,9 +188,10 @@ __device__ __forceinline__ double rnd32(double v) { return (double)(float)v; }
 // separation d by up to ~|s| 2^-24 and its 1/d^2 term by three times that relative to d:
 // for the rare pairs much closer than the mean spacing this is the dominant error of an
 // ion's force.  Every live ion is entered, at the end of the push (or whenever the FP32
-// positions are rewritten), into a hashed grid of cells at least as wide as the
-// correction distance; the kick walks the 27 cells around each ion and replaces the
-// FP32-position value of every pair closer than that distance by its FP64 value.
+// positions are rewritten), into a hashed grid of cells a little wider than twice the
+// correction distance; the kick walks the 2 x 2 x 2 cells nearest to each ion (which
+// hold every ion within that distance) and replaces the FP32-position value of every
+// pair closer than it by its FP64 value.
 // A bucket word is (epoch << 32) | first ion; entries of another epoch read as empty, so
 // the grid is never cleared.  Ctrl::cp_epoch is the epoch of the last complete build
 // (the one the kick reads); a build enters its ions under the next epoch and publishes it
@@ -240,7 +241,11 @@ __device__ void close_pair_corr(const unsigned long long* __restrict__ head, con
                                 PosF pos, double& cx, double& cy, double& cz)
 {
     const float4 fi = fpos[i];
-    const int c0x = cp_cell(fi.x, hinv), c0y = cp_cell(fi.y, hinv), c0z = cp_cell(fi.z, hinv);
+    // lower corner of the 2 x 2 x 2 cells around the ion: towards the nearer cell face
+    const float ux = fi.x * hinv, uy = fi.y * hinv, uz = fi.z * hinv;
+    const int c0x = __float2int_rd(ux), c0y = __float2int_rd(uy), c0z = __float2int_rd(uz);
+    const int lx = c0x - (ux - (float)c0x < 0.5f), ly = c0y - (uy - (float)c0y < 0.5f),
+              lz = c0z - (uz - (float)c0z < 0.5f);
     const double sxi = xi * ls_inv, syi = yi * ls_inv, szi = zi * ls_inv;
     int keep[CP_KEEP];
     int nclose = 0;
@@ -273,10 +278,10 @@ __device__ void close_pair_corr(const unsigned long long* __restrict__ head, con
             break;
         }
         int found = 0;
-        for (int dz = -1; dz <= 1; ++dz)
-            for (int dy = -1; dy <= 1; ++dy)
-                for (int dx = -1; dx <= 1; ++dx) {
-                    const int cx_ = c0x + dx, cy_ = c0y + dy, cz_ = c0z + dz;
+        for (int dz = 0; dz < 2; ++dz)
+            for (int dy = 0; dy < 2; ++dy)
+                for (int dx = 0; dx < 2; ++dx) {
+                    const int cx_ = lx + dx, cy_ = ly + dy, cz_ = lz + dz;
                     const unsigned long long hw = head[cp_bucket(cx_, cy_, cz_, mask)];
                     if ((unsigned)(hw >> 32) != epoch) continue;
                     int j = (int)(unsigned)hw;

@@ -194,6 +194,9 @@ int launch_push_scan(const Phys& P, const Bufs& B, cudaStream_t s);
 int launch_forces(const Phys& P, const Bufs& B, const ForceArgs& F, int variant, cudaStream_t s);
 int launch_kick(const Phys& P, const Bufs& B, const ForceArgs& F, int mode, cudaStream_t s);
 int launch_cp_bump(const Bufs& B, cudaStream_t s);  // advance the close-pair list epoch
+// OML floating charge of every grain into Ctrl::Q (nq Gauss-Legendre nodes glx, glw on [-1, 1])
+int launch_oml_charge(const Phys& P, const Bufs& B, double n_inf, double m_i, double Z, double T_e, int nq,
+                      const double* glx, const double* glw, cudaStream_t s);
 int launch_forces_f64(const Phys& P, const Bufs& B, int after_push, cudaStream_t s);
 int launch_dust(const Phys& P, const Bufs& B, int mode, cudaStream_t s);
 int launch_stats(const Phys& P, const Bufs& B, double* mean_se, cudaStream_t s);

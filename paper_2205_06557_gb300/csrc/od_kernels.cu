@@ -187,6 +187,93 @@ __global__ void k_eout_grid(double R, double H, double lam, int nx, int nz, int 
     }
 }
 
+// ------------------------------------------------ OML floating charge (Sec. 2 "oml")
+// One CTA per grain.  The floating potential phi <= 0 balances the OML ion current of a
+// drifting Maxwellian (thermal speed sig, drift u; cross-section pi a^2 (1 - 2 Z e phi /
+// (m v^2))) against the Boltzmann electron current
+//   I_e = e Z n pi a^2 sqrt(8 k T_e / (pi m_e)) exp(e phi / k T_e);
+// the ion current is one speed integral of v^3 sigma(v) times the angular average of the
+// shifted Maxwellian, Gauss-Legendre on [0, u] and [u, u + 14 sig] (the nodes split over
+// the CTA, summed in a fixed order).  Bisection on [-200 k T_e / e, 0] to 1e-14 k T_e / e;
+// Q = 4 pi eps0 a phi.
+constexpr int OML_BT = 256;
+
+struct OmlArgs {
+    double n, m, sig, u, Z, kTe_over_e, Ie_coef;  // Ie_coef = e Z n sqrt(8 k T_e / (pi m_e)) pi
+    int D;
+    double a[MAXD];
+};
+
+__device__ double oml_block_sum(double v, double* s_w)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if (lane == 0) s_w[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int k = 0; k < OML_BT / 32; ++k) t += s_w[k];
+    return t;
+}
+
+__global__ void __launch_bounds__(OML_BT) k_oml_charge(OmlArgs A, int nq, const double* __restrict__ glx,
+                                                     const double* __restrict__ glw, Ctrl* C)
+{
+    __shared__ double s_w[OML_BT / 32];
+    const int k = blockIdx.x;
+    const double a = A.a[k], PI = 3.141592653589793, QE = 1.602176634e-19, EPS0 = 8.8541878128e-12;
+    const double s2 = A.sig * A.sig;
+    const int nseg = A.u > 0.0 ? 2 : 1;
+    const double e0 = 0.0, e1 = A.u > 0.0 ? A.u : 0.0, e2 = e1 + 14.0 * A.sig;
+    const double norm = A.Z * QE * A.n * pow(2.0 * PI * s2, -1.5);
+    double lo = -200.0 * A.kTe_over_e, hi = 0.0;
+    for (int it = 0; it < 200 && hi - lo > 1e-14 * A.kTe_over_e; ++it) {
+        const double phi = 0.5 * (lo + hi);
+        double part = 0.0;
+        for (int q = threadIdx.x; q < nseg * nq; q += OML_BT) {
+            const int seg = q / nq, iq = q % nq;
+            const double pa = seg == 0 ? (nseg == 2 ? e0 : e0) : e1, pb = seg == 0 ? (nseg == 2 ? e1 : e2) : e2;
+            const double v = 0.5 * (pa + pb) + 0.5 * (pb - pa) * glx[iq];
+            const double wv = 0.5 * (pb - pa) * glw[iq];
+            if (!(v > 0.0)) continue;
+            const double cross = PI * a * a * (1.0 - 2.0 * A.Z * QE * phi / (A.m * v * v));
+            double ang;
+            if (A.u <= 0.0) {
+                ang = 4.0 * PI * exp(-v * v / (2.0 * s2));
+            } else {
+                const double x = v * A.u / s2;
+                ang = 2.0 * PI * (exp(-(v - A.u) * (v - A.u) / (2.0 * s2)) - exp(-(v + A.u) * (v + A.u) / (2.0 * s2))) / x;
+            }
+            part += wv * v * v * v * cross * ang;
+        }
+        const double Ii = norm * oml_block_sum(part, s_w);
+        const double Ie = A.Ie_coef * a * a * exp(phi / A.kTe_over_e);
+        if (Ii - Ie > 0.0) lo = phi;
+        else hi = phi;
+    }
+    if (threadIdx.x == 0) C->Q[k] = 4.0 * PI * EPS0 * a * 0.5 * (lo + hi);
+}
+
+int launch_oml_charge(const Phys& P, const Bufs& B, double n_inf, double m_i, double Z, double T_e, int nq,
+                      const double* glx, const double* glw, cudaStream_t s)
+{
+    if (P.D == 0) return 0;
+    OmlArgs A{};
+    const double KB = 1.380649e-23, QE = 1.602176634e-19, ME = 9.1093837015e-31, PI = 3.141592653589793;
+    A.n = n_inf;
+    A.m = m_i;
+    A.sig = P.sig;
+    A.u = P.u;
+    A.Z = Z;
+    A.kTe_over_e = KB * T_e / QE;
+    A.Ie_coef = QE * Z * n_inf * sqrt(8.0 * KB * T_e / (PI * ME)) * PI;
+    A.D = P.D;
+    for (int k = 0; k < P.D; ++k) A.a[k] = P.ga[k];
+    k_oml_charge<<<P.D, OML_BT, 0, s>>>(A, nq, glx, glw, B.ctrl);
+    return (int)cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- launchers
 static int ck(cudaError_t e)
 {
@@ -505,13 +592,13 @@ static_assert((kStaticBuckets & (kStaticBuckets - 1)) == 0, "bucket count must b
 static __device__ __align__(256) float4 g_static_scratch[kStaticFloat4];
 
 // correction distance and cell width (scaled units) from the largest |s|: pairs closer
-// than 0.005 max(1, |s|max) get their FP64 value
+// than 0.005 max(1, |s|max / 4) get their FP64 value (cells 2.1 times as wide)
 __device__ __forceinline__ void static_cp_params(const unsigned* bound, double& dc2, float& hinv)
 {
     const double smax = (double)__uint_as_float(*bound);
-    const double dc = 0.005 * fmax(1.0, smax);
+    const double dc = 0.005 * fmax(1.0, 0.25 * smax);
     dc2 = dc * dc;
-    hinv = (float)(1.0 / (1.05 * dc));
+    hinv = (float)(1.0 / (2.1 * dc));
 }
 
 // largest |coordinate| in scaled units (non-negative floats order like their bits)

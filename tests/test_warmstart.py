@@ -1,6 +1,7 @@
 """Warm-start pipeline: host-side pieces on CPU (features, targets, convergence
 criterion), and a small end-to-end run on the GPU showing what the trained network
-gains over starting the consistent charge iteration from zero."""
+gains over starting the consistent charge iteration from zero and from the OML charge
+(the usual starting point)."""
 import math
 
 import numpy as np
@@ -57,19 +58,25 @@ def test_force_convergence_criterion():
 
 
 @pytest.mark.gpu
-def test_warm_start_pipeline_beats_zero_start():
+def test_warm_start_pipeline_beats_zero_and_oml_starts():
     from paper_2205_06557_gb300 import warmstart as ws
 
     # a dense plasma (charging time ~2,400 steps) in a small domain (~6,000 ions) keeps
     # the label and evaluation runs short enough to converge in a test
     dom = dict(n_inf=1e15, R=1e-4, H=2e-4)
-    plist, X, M, T = ws.generate(48, 10000, seed0=0, batch_runs=48, **dom)
-    assert X.shape == (48, 8, 7) and np.isfinite(T).all()
-    net, norm, losses, vlosses = ws.train(X, M, T, iters=400, batch=32)
+    plist, X, M, T = ws.generate(96, 10000, seed0=0, batch_runs=96, **dom)
+    assert X.shape == (96, 8, 7) and np.isfinite(T).all()
+    net, norm, losses, vlosses = ws.train(X, M, T, iters=800, batch=32)
     assert losses[-30:].mean() < losses[:30].mean()
-    evalp = [ws.study_run(10_000 + s, 8000, **dom) for s in range(6)]
+    evalp = [ws.study_run(10_000 + s, 8000, **dom) for s in range(8)]
     steps, err0 = ws.evaluate(net, norm, evalp, 8000, tol=0.02)
-    # starting from zero charge is far from converged; the network starts close
+    print("WARMSTART median initial charge error zero %.3f oml %.3f net %.3f; median steps to 2%% zero %d oml %d "
+          "net %d" % (np.median(err0["zero"]), np.median(err0["oml"]), np.median(err0["net"]),
+                      np.median(steps["zero"]), np.median(steps["oml"]), np.median(steps["net"])))
+    # starting from zero charge is far from converged; the network starts closer than the
+    # OML charge and reaches the converged charge in fewer steps (median over the grains)
     assert np.median(err0["net"]) < 0.2 * np.median(err0["zero"])
     assert steps["net"].mean() < steps["zero"].mean()
+    assert np.median(err0["net"]) < np.median(err0["oml"])
+    assert np.median(steps["net"]) < np.median(steps["oml"])
     net.close()
