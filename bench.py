@@ -86,6 +86,11 @@ def parse():
     ap.add_argument("--eval-runs", type=int, default=48)
     ap.add_argument("--eval-steps", type=int, default=100000)
     ap.add_argument("--runs", type=int, default=64)
+    ap.add_argument("--ws-plasma", default="dense", choices=["dense", "2e14"],
+                    help="warm-start study plasma: 'dense' = 1e15 m^-3 in R = 0.1 mm, H = 0.2 mm (~6,300 ions, "
+                         "charging time ~2,400 steps); '2e14' = 2e14 m^-3 in R = 0.12 mm, H = 0.24 mm (~2,200 ions)")
+    ap.add_argument("--chain-eval-runs", type=int, default=3)
+    ap.add_argument("--chain-eval-steps", type=int, default=10000)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -375,7 +380,7 @@ def run_ours(args):
         "ion_steps_per_s": world * float(N) * args.steps / (t_max / 1e3),
         "wall_s_timed": wall,
         "kernel_ms_per_step": {"push_scan_inject": kms[0] / max(kn[0], 1), "pair_forces": k1_ms,
-                               "kick_collide": kms[2] / max(kn[2], 1), "grain_update": kms[3] / max(kn[3], 1)},
+                               "kick_collide_grain_update": kms[2] / max(kn[2], 1)},
         "roofline": {"bound": "alu", "kernel": kname, "achieved": k1_rate / 1e9, "peak": peak / 1e9,
                      "unit": "Gpair/s", "frac": k1_rate / peak, "traffic": ncu_traffic(kname, N),
                      "algorithmic_bytes": N * (16 + (24 if sym else 16)),
@@ -383,7 +388,7 @@ def run_ours(args):
                                    % (sms, clk_max, PAIRS_PER_CLK_SM[sym],
                                       "17 FP32 + rsqrt + ex2 per unordered pair" if sym else "14 FP32 + rsqrt + ex2 per pair")},
         "clocks": clk,
-        "gpu_launches": 4 * args.steps * world,
+        "gpu_launches": 5 * args.steps * world,  # scan, pair forces, kick with the grain tail, and the two kernels beside the pair forces
         "e2e": {"value": e2e_units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
     }
     if world == 1 and not args.no_cpu_baseline:
@@ -451,8 +456,9 @@ def run_warmstart(args):
     world, rank, local = dist_env()
     torch.cuda.set_device(local)
     # Debye-scaled domain at 2e14 m^-3 (R = 0.16 lambda_De as in the ~2,000-ion workload's
-    # 0.12): charging times <= ~2.2e4 steps, so labels converge within the run
-    dom = dict(n_inf=2e14, R=1.2e-4, H=2.4e-4)
+    # 0.12): charging times <= ~2.2e4 steps; or the denser 1e15 m^-3 plasma (charging times
+    # ~2,400 steps), whose shorter label runs allow ~20,000 grain samples
+    dom = dict(n_inf=1e15, R=1e-4, H=2e-4) if args.ws_plasma == "dense" else dict(n_inf=2e14, R=1.2e-4, H=2.4e-4)
     t0 = time.perf_counter()
     plist, X, M, T = ws.generate(args.runs, args.label_steps, seed0=rank * 100_000, **dom)
     t_gen = time.perf_counter() - t0
@@ -481,9 +487,45 @@ def run_warmstart(args):
     wall_f = {"plain_single_run_zero_start": float(np.mean(steps_f["zero"])) * t_single,
               "plain_single_run_oml_start": float(np.mean(steps_f["oml"])) * t_single,
               "batched_network_start": float(np.mean(steps_f["net"])) * per_run}
+    # held-out dust-chain runs (2-8 grains on the axis of an elongated domain, ~85,000 ions
+    # at the dense plasma): each started three ways in one batch, the plain method from the
+    # OML charge also timed alone
+    chain = None
+    if args.chain_eval_runs > 0:
+        cdom = dict(n_inf=dom["n_inf"], R=1.5 * dom["R"], H=12.0 * 0.5 * dom["H"])
+        cps = [ws.chain_run(rank * 100_000 + 80_000 + s, args.chain_eval_steps, **cdom)
+               for s in range(args.chain_eval_runs)]
+        t0 = time.perf_counter()
+        c_steps, c_err0, c_steps_f, c_tb = ws.evaluate(net, norm, cps, args.chain_eval_steps, tol=0.01, details=True)
+        t_chain = time.perf_counter() - t0
+        one = od.Run(cps[0])
+        one.step(20)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        one.step(200)
+        c_single = (time.perf_counter() - t0) / 200
+        n_chain = one.N
+        one.close()
+        c_per_run = c_tb / (3 * len(cps))
+        chain = {"runs": len(cps), "grains": int(len(c_steps["net"])), "ions_first_run": n_chain,
+                 "grains_per_run": [len(p["dust"]) for p in cps], "steps": args.chain_eval_steps,
+                 "domain": "R = %.2f mm, H = %.2f mm, n = %.0e m^-3" % (1e3 * cdom["R"], 1e3 * cdom["H"], cdom["n_inf"]),
+                 "steps_mean": {k: float(np.mean(v)) for k, v in c_steps.items()},
+                 "steps_median": {k: float(np.median(v)) for k, v in c_steps.items()},
+                 "not_converged_fraction": {k: float(np.mean(v >= args.chain_eval_steps)) for k, v in c_steps.items()},
+                 "initial_charge_error_median": {k: float(np.median(v)) for k, v in c_err0.items()},
+                 "force_steps_mean": {k: float(np.mean(v)) for k, v in c_steps_f.items()},
+                 "step_time_s": {"single_run": c_single, "batched_per_run": c_per_run},
+                 "wall_s_per_run_to_converged_charge": {
+                     "plain_single_run_oml_start": float(np.mean(c_steps["oml"])) * c_single,
+                     "plain_single_run_zero_start": float(np.mean(c_steps["zero"])) * c_single,
+                     "batched_network_start": float(np.mean(c_steps["net"])) * c_per_run},
+                 "wall_s": t_chain}
+    plasma = ("~6,300-ion runs (n=1e15 m^-3, R=0.1 mm, H=0.2 mm)" if args.ws_plasma == "dense"
+              else "~2,200-ion runs (n=2e14 m^-3, R=0.12 mm, H=0.24 mm)")
     line = {"metric": "time-to-converged dust charge (steps to stay within 1%)", "unit": "steps",
             "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
-            "config": {"workload": "~2,200-ion runs (n=2e14 m^-3, R=0.12 mm, H=0.24 mm), Ar+ 300 K, T_e 2 eV, "
+            "config": {"workload": plasma + ", Ar+ 300 K, T_e 2 eV, "
                                    "Mach U(0.3, 2), nu in {1e5, 1e6, 5e6} /s, "
                                    "1-4 grains of radius U(10, 20) um, consistent charging",
                        "train_runs": args.runs, "label_steps": args.label_steps, "train_grains": int(M.sum()),
@@ -508,7 +550,8 @@ def run_warmstart(args):
             "wall_speedup_force_vs_plain_oml": wall_f["plain_single_run_oml_start"] / max(wall_f["batched_network_start"], 1e-30),
             "train_loss_first_last": [float(losses[:50].mean()), float(losses[-50:].mean())],
             "validation_loss_best": float(vlosses.min()) if len(vlosses) else None,
-            "wall_s": {"generate": t_gen, "train": t_train, "evaluate": t_eval}}
+            "wall_s": {"generate": t_gen, "train": t_train, "evaluate": t_eval},
+            "chain_runs": chain}
     net.close()
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -220,7 +220,8 @@ int od_info(od_handle* h, double* out);
  * at a time and at the end of the call (the host does not wait between steps, so the
  * device runs them back to back; results are bit-identical to the graph replay).
  * od_set_profiling resets the sums. od_kernel_times: ms[4] and launches[4] for
- * push+scan+inject, pair forces, kick+collide, grain update. Host arrays. */
+ * push+scan+inject, pair forces, kick+collide with the grain update (which runs in the
+ * kick's last block), and a fourth entry kept at zero time. Host arrays. */
 int od_set_profiling(od_handle* h, int on);
 int od_kernel_times(od_handle* h, double* ms, int64_t* launches);
 

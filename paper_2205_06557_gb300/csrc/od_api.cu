@@ -613,8 +613,7 @@ int force_eval(od_handle* h)
 {
     OD_LK(h, launch_fpos(h->P, h->B, (int)(h->host_step & 1), h->stream));
     OD_LK(h, launch_pairs(h, 0));
-    OD_LK(h, launch_kick(h->P, h->B, h->F, 1, h->stream));
-    OD_LK(h, launch_dust(h->P, h->B, 1, h->stream));
+    OD_LK(h, launch_kick(h->P, h->B, h->F, 1, h->stream));  // with the grain tail
     return OD_OK;
 }
 
@@ -626,12 +625,45 @@ int launch_density(od_handle* h)
     return OD_OK;
 }
 
+// the next step's injection samples on the second stream, beside the pair forces (fork
+// after the scan, which fixes their ids; joined by join_ahead before the step ends)
+// and this step's collision velocities on a third (joined by join_collide before the kick)
+int fork_ahead(od_handle* h)
+{
+    if (!h->aux) return OD_OK;
+    OD_CK(h, cudaEventRecord(h->ev_fork, h->stream));
+    OD_CK(h, cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
+    OD_LK(h, launch_inject_ahead(h->P, h->B, h->aux));
+    OD_CK(h, cudaEventRecord(h->ev_join, h->aux));
+    OD_CK(h, cudaStreamWaitEvent(h->aux2, h->ev_fork, 0));
+    OD_LK(h, launch_collide_ahead(h->P, h->B, h->aux2));
+    OD_CK(h, cudaEventRecord(h->ev_join2, h->aux2));
+    return OD_OK;
+}
+
+int join_collide(od_handle* h)
+{
+    if (!h->aux) return OD_OK;
+    OD_CK(h, cudaStreamWaitEvent(h->stream, h->ev_join2, 0));
+    return OD_OK;
+}
+
+int join_ahead(od_handle* h)
+{
+    if (!h->aux) return OD_OK;
+    OD_CK(h, cudaStreamWaitEvent(h->stream, h->ev_join, 0));
+    return OD_OK;
+}
+
 int launch_step(od_handle* h)
 {
+    int rc;
     OD_LK(h, launch_push_scan(h->P, h->B, h->stream));
+    if ((rc = fork_ahead(h))) return rc;
     OD_LK(h, launch_pairs(h, 1));
-    OD_LK(h, launch_kick(h->P, h->B, h->F, 0, h->stream));
-    OD_LK(h, launch_dust(h->P, h->B, 0, h->stream));
+    if ((rc = join_collide(h))) return rc;
+    OD_LK(h, launch_kick(h->P, h->B, h->F, 0, h->stream));  // with the grain tail
+    if ((rc = join_ahead(h))) return rc;
     return launch_density(h);
 }
 
@@ -734,6 +766,13 @@ void free_all(od_handle* h)
         if (e) cudaEventDestroy(e);
     for (auto& e : h->pev)
         if (e) cudaEventDestroy(e);
+    cudaFree(h->B.inj_ahead);
+    cudaFree(h->B.coll_v);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
+    if (h->ev_join2) cudaEventDestroy(h->ev_join2);
+    if (h->aux) cudaStreamDestroy(h->aux);
+    if (h->aux2) cudaStreamDestroy(h->aux2);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
 }
 
@@ -790,12 +829,15 @@ int create_impl(const od_params* p, od_handle* h)
     OD_CK(h, cudaMalloc(&B.acc, sizeof(float4) * h->npad_cap));
     OD_CK(h, cudaMalloc(&B.fpos, sizeof(float4) * h->npad_cap));
     // fixed-point pair sums [3][npad_cap] (zero between evaluations) and the close-pair
-    // cell buckets (a power of two, at least twice the capacity) and links
+    // cell buckets (a power of two) and links
     B.psum_ld = h->npad_cap;
     OD_CK(h, cudaMalloc(&B.psum, sizeof(long long) * 3 * h->npad_cap));
     OD_CK(h, cudaMemsetAsync(B.psum, 0, sizeof(long long) * 3 * h->npad_cap, h->stream));
+    // (eight buckets per ion up to 2^18 ions: the walks then meet few ions of other cells;
+    // two per ion above, which keeps the grid near the L2's size)
     unsigned long long nbk = 1024;
-    while (nbk < 2ull * (unsigned long long)h->cap) nbk <<= 1;
+    const unsigned long long want = (h->cap <= (1 << 18) ? 8ull : 2ull) * (unsigned long long)h->cap;
+    while (nbk < want) nbk <<= 1;
     h->P.cp_mask = (unsigned)(nbk - 1);
     OD_CK(h, cudaMalloc(&B.cp_head, sizeof(unsigned long long) * nbk));
     OD_CK(h, cudaMemsetAsync(B.cp_head, 0, sizeof(unsigned long long) * nbk, h->stream));
@@ -808,6 +850,17 @@ int create_impl(const od_params* p, od_handle* h)
     OD_CK(h, cudaMemsetAsync(B.tile_status, 0, sizeof(unsigned long long) * ntiles, h->stream));
     OD_CK(h, cudaMalloc(&B.inj, sizeof(Inj) * h->cap));
     OD_CK(h, cudaMalloc(&B.rem, sizeof(Rem) * h->cap));
+    OD_CK(h, cudaMalloc(&B.inj_ahead, sizeof(Inj) * INJ_AHEAD));
+    if (!h->batch_member) {
+        // single runs draw the next step's injection samples and this step's collision
+        // velocities on two more streams, beside the pair forces
+        OD_CK(h, cudaMalloc(&B.coll_v, sizeof(double) * 3 * h->cap));
+        OD_CK(h, cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking));
+        OD_CK(h, cudaStreamCreateWithFlags(&h->aux2, cudaStreamNonBlocking));
+        OD_CK(h, cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+        OD_CK(h, cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+        OD_CK(h, cudaEventCreateWithFlags(&h->ev_join2, cudaEventDisableTiming));
+    }
     OD_CK(h, cudaMalloc(&B.dpart, sizeof(double) * h->nb_cap * MAXD * 3));
     OD_CK(h, cudaMalloc(&B.ctrl, sizeof(Ctrl)));
     OD_CK(h, cudaMalloc(&h->d_stats, sizeof(double) * 2 * MAXD * REC));
@@ -923,12 +976,14 @@ int od_step(od_handle* h, int64_t n)
                 OD_CK(h, cudaEventRecord(e[0], h->stream));
                 OD_LK(h, launch_push_scan(h->P, h->B, h->stream));
                 OD_CK(h, cudaEventRecord(e[1], h->stream));
+                if ((rc = fork_ahead(h))) return rc;
                 OD_LK(h, launch_pairs(h, 1));
                 OD_CK(h, cudaEventRecord(e[2], h->stream));
-                OD_LK(h, launch_kick(h->P, h->B, h->F, 0, h->stream));
+                if ((rc = join_collide(h))) return rc;
+                OD_LK(h, launch_kick(h->P, h->B, h->F, 0, h->stream));  // with the grain tail
                 OD_CK(h, cudaEventRecord(e[3], h->stream));
-                OD_LK(h, launch_dust(h->P, h->B, 0, h->stream));
                 OD_CK(h, cudaEventRecord(e[4], h->stream));
+                if ((rc = join_ahead(h))) return rc;
                 if ((rc = launch_density(h))) return rc;
                 if (++h->pev_used == PROF_RING && (rc = drain_profile(h))) return rc;
             } else {

@@ -66,32 +66,25 @@ __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, double& n0, d
 __device__ __forceinline__ double ncdf(double z) { return 0.5 * erfc(-z * 0.70710678118654752); }
 __device__ __forceinline__ double npdf(double z) { return exp(-0.5 * z * z) * 0.39894228040143268; }
 
-// flux through the bottom face up to axial speed v: int_0^v v' N(v'; u, s^2) dv'
-static __device__ double flux_bottom(double v, double u, double s)
-{
-    const double z = (v - u) / s, z0 = -u / s;
-    return u * (ncdf(z) - ncdf(z0)) + s * (npdf(z0) - npdf(z));
-}
-
-// flux through the top face from axial speed v < 0 up to 0: -int_v^0 v' N(v'; u, s^2) dv'
-static __device__ double flux_top(double v, double u, double s)
-{
-    const double z = (v - u) / s, z0 = -u / s;
-    return -u * (ncdf(z0) - ncdf(z)) + s * (npdf(z0) - npdf(z));
-}
-
-// Invert a monotone flux CDF F on [lo, hi] for the value target: Newton steps on
-// F(v) - target with derivative |v| N(v; u, s^2), kept inside a shrinking bracket
-// (bisection when a step leaves it).
+// Invert a monotone App. B flux CDF on [lo, hi] for the value target: Newton steps with
+// derivative |v| N(v; u, s^2), kept inside a shrinking bracket (bisection when a step
+// leaves it).  The bottom face's flux up to axial speed v is
+//   int_0^v v' N(v'; u, s^2) dv' = u (Phi(z) - Phi(z0)) + s (phi(z0) - phi(z)),
+// the top face's from v < 0 up to 0 is -u (Phi(z0) - Phi(z)) + s (phi(z0) - phi(z)), with
+// z = (v - u) / s, z0 = -u / s (Phi, phi the standard normal CDF and density); Phi(z0)
+// and phi(z0) are evaluated once per sample, Phi(z) and phi(z) once per iteration.
 template <bool TOP>
 __device__ double invert_flux(double target, double lo, double hi, double v, double u, double s)
 {
+    const double z0 = -u / s, c0 = ncdf(z0), p0 = npdf(z0);
     for (int it = 0; it < 100; ++it) {
-        const double F = TOP ? flux_top(v, u, s) : flux_bottom(v, u, s);
+        const double z = (v - u) / s;
+        const double cz = ncdf(z), pz = npdf(z);
+        const double F = TOP ? -u * (c0 - cz) + s * (p0 - pz) : u * (cz - c0) + s * (p0 - pz);
         const double g = TOP ? (target - F) : (F - target);  // increasing in v
         if (g < 0) lo = v;
         else hi = v;
-        const double dg = fabs(v) * npdf((v - u) / s) / s;
+        const double dg = fabs(v) * pz / s;
         // converged once the Newton correction is below ~1e-13 of the speed scale; the
         // check comes before the bracket test, which a sub-ulp step would fail
         const double tol = 1e-13 * fmax(fabs(v), s);
@@ -156,6 +149,36 @@ static __device__ void sample_injection(const Phys& P, unsigned long long id, ui
         o.face = 2;
     }
     o.id = id;
+}
+
+// The App. B sample of the ion with this id entering in step sn: computed ahead (during
+// the previous step, beside the pair forces) when it is there, else now.  A sample is a
+// function of (seed, id, sn) and the run's constants only, so both give the same bits.
+static __device__ __forceinline__ void injection_for(const Phys& P, const Bufs& B, const Ctrl* C,
+                                                     unsigned long long base, int r, uint32_t sn, Inj& o)
+{
+    if (r < C->ahead_n && C->ahead_base == base && C->ahead_sn == (long long)sn) {
+        const Inj* a = B.inj_ahead + r;
+        o.x = __ldcg(&a->x), o.y = __ldcg(&a->y), o.z = __ldcg(&a->z);
+        o.vx = __ldcg(&a->vx), o.vy = __ldcg(&a->vy), o.vz = __ldcg(&a->vz);
+        o.id = __ldcg(&a->id);
+        o.face = __ldcg(&a->face);
+    } else {
+        sample_injection(P, base + (unsigned long long)r, sn, o);
+    }
+}
+
+// Andersen collision: a zero-mean Maxwellian velocity at the neutral temperature
+__device__ __forceinline__ void collision_velocity(const Phys& P, unsigned long long id, uint32_t sn, double& vx,
+                                                   double& vy, double& vz)
+{
+    const uint4 wv = philox(P, id, sn, ST_COLL_VEL);
+    double n0, n1, n2, n3;
+    box_muller(wv.x, wv.y, n0, n1);
+    box_muller(wv.z, wv.w, n2, n3);
+    vx = P.sig_n * n0;
+    vy = P.sig_n * n1;
+    vz = P.sig_n * n2;
 }
 
 // E_out = -grad P (App. A): E = (-x G, -y G, -z K), G and K over monomials r2^p z2^q, p+q <= 3
@@ -226,13 +249,46 @@ __device__ __forceinline__ void pair_term_f64(double dx, double dy, double dz, d
 }
 
 // Close-pair correction of target i, in scaled units: the sum over ions j with
-// |s_j - s_i| < sqrt(dc2) (FP64 positions) of T(d) - T(d~), T the pair term, d the FP64
-// separation and d~ = fpos_j - fpos_i the separation the FP32 kernels used.  The sum is
-// made order-independent (the lists' order depends on the atomics that built them): the
-// terms are rounded to a common power-of-two grid set by the largest of them and added as
-// integers.  pos(j, x, y, z) gives the FP64 (unscaled) position of ion j; at most
-// CP_KEEP close pairs are kept for the second pass, more are found again.
-constexpr int CP_KEEP = 4;
+// |s_j - s_i| < sqrt(dc2) of T(d) - T(d~), T the pair term, d the FP64 separation and
+// d~ = fpos_j - fpos_i the separation the FP32 kernels used.  The difference is the
+// first-order change of T over delta = d - d~ (computed in FP64, exact up to its last
+// bits), evaluated in FP32 at d~:
+//   T(d) - T(d~) = c delta + (c'(s) / s) (d~ . delta) d~,  c = (1 + s ln2) 2^-s / s^3,
+//   c'(s) / s = -2^-s (3 (1 + s ln2) + (s ln2)^2) / s^5,  s = |d~|;
+// it is exact up to (|delta| / s)^2 of T, so pairs with |delta| > 1e-4 s (two ions far
+// closer than their rounding would allow at that |s|) take the FP64 difference of the two
+// terms instead.  The corrections are added in ascending j (the lists' order depends on
+// the atomics that built them), so the sum is deterministic.  pos(j, x, y, z) gives the
+// FP64 (unscaled) position of ion j.
+constexpr int CP_KEEP = 8;
+
+__device__ __forceinline__ void close_pair_term(float4 fi, float4 fj, double ex, double ey, double ez, float3& t)
+{
+    // delta = d - d~ (FP64, exact difference of the FP32 values)
+    const double gx = (double)fj.x - (double)fi.x, gy = (double)fj.y - (double)fi.y, gz = (double)fj.z - (double)fi.z;
+    const double dx = ex - gx, dy = ey - gy, dz = ez - gz;
+    const double s2 = gx * gx + gy * gy + gz * gz;
+    if (dx * dx + dy * dy + dz * dz > 1e-8 * s2) {
+        double t0x, t0y, t0z, t1x, t1y, t1z;
+        pair_term_f64(ex, ey, ez, t0x, t0y, t0z);
+        pair_term_f64(gx, gy, gz, t1x, t1y, t1z);
+        t = make_float3((float)(t0x - t1x), (float)(t0y - t1y), (float)(t0z - t1z));
+        return;
+    }
+    constexpr float LN2 = 0.69314718055994531f;
+    const float qx = (float)gx, qy = (float)gy, qz = (float)gz;
+    const float q2 = fmaf(qx, qx, fmaf(qy, qy, qz * qz));
+    const float ri = rsqrt_approx(q2);
+    const float sd = q2 * ri;  // s
+    const float e = ex2_approx(-sd);
+    const float sl = sd * LN2;
+    const float ri2 = ri * ri;
+    const float c = e * ri2 * ri * (1.f + sl);
+    const float cp = -e * (ri2 * ri2 * ri) * fmaf(sl, sl, 3.f * (1.f + sl));
+    const float fx = (float)dx, fy = (float)dy, fz = (float)dz;
+    const float proj = cp * fmaf(qx, fx, fmaf(qy, fy, qz * fz));
+    t = make_float3(fmaf(c, fx, proj * qx), fmaf(c, fy, proj * qy), fmaf(c, fz, proj * qz));
+}
 
 template <class PosF>
 __device__ void close_pair_corr(const unsigned long long* __restrict__ head, const int* __restrict__ next,
@@ -246,78 +302,68 @@ __device__ void close_pair_corr(const unsigned long long* __restrict__ head, con
     const int c0x = __float2int_rd(ux), c0y = __float2int_rd(uy), c0z = __float2int_rd(uz);
     const int lx = c0x - (ux - (float)c0x < 0.5f), ly = c0y - (uy - (float)c0y < 0.5f),
               lz = c0z - (uz - (float)c0z < 0.5f);
-    const double sxi = xi * ls_inv, syi = yi * ls_inv, szi = zi * ls_inv;
-    int keep[CP_KEEP];
-    int nclose = 0;
-    double big = 0.0;
-    // pass 1 (pass 2 only when more than CP_KEEP pairs were found): find the close pairs
-    // and the largest correction component; pass 2 adds them on the integer grid
-    long long qx = 0, qy = 0, qz = 0;
-    double grid = 0.0;
-    for (int pass = 0; pass < 2; ++pass) {
-        if (pass == 1) {
-            if (nclose == 0) break;
-            int e;
-            frexp(big, &e);
-            grid = ldexp(1.0, 52 - e);  // |term| * grid < 2^52: up to 2^11 terms without overflow
-        }
-        if (pass == 1 && nclose <= CP_KEEP) {
-            for (int k = 0; k < nclose; ++k) {
-                const int j = keep[k];
+    const float dc2_f = (float)(1.01 * dc2);
+    int kj[CP_KEEP];
+    float3 kt[CP_KEEP];
+    int n = 0, over = 0;
+    int last = -1;  // with more than CP_KEEP close pairs: the pairs up to j = last are summed
+    cx = cy = cz = 0.0;
+    // the eight bucket words are loaded at once (one memory round trip, not eight)
+    unsigned long long hws[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) hws[c] = head[cp_bucket(lx + (c & 1), ly + ((c >> 1) & 1), lz + (c >> 2), mask)];
+    for (int round = 0; round < n_live; ++round) {
+        n = 0;
+        over = 0;
+#pragma unroll 1
+        for (int c = 0; c < 8; ++c) {
+            const int cx_ = lx + (c & 1), cy_ = ly + ((c >> 1) & 1), cz_ = lz + (c >> 2);
+            const unsigned long long hw = hws[c];
+            if ((unsigned)(hw >> 32) != epoch) continue;
+            int j = (int)(unsigned)hw;
+            for (int guard = 0; j >= 0 && j < n_live && guard < n_live; ++guard, j = next[j]) {
+                if (j == i || j <= last) continue;
+                const float4 fj = fpos[j];
+                if (cp_cell(fj.x, hinv) != cx_ || cp_cell(fj.y, hinv) != cy_ || cp_cell(fj.z, hinv) != cz_)
+                    continue;  // another cell sharing the bucket
+                // FP32 pre-test on the rounded separation (a 1% margin in d^2 covers its rounding)
+                const float gx = fj.x - fi.x, gy = fj.y - fi.y, gz = fj.z - fi.z;
+                if (fmaf(gx, gx, fmaf(gy, gy, gz * gz)) > dc2_f) continue;
                 double xj, yj, zj;
                 pos(j, xj, yj, zj);
-                const float4 fj = fpos[j];
-                double t0x, t0y, t0z, t1x, t1y, t1z;
-                pair_term_f64(xj * ls_inv - sxi, yj * ls_inv - syi, zj * ls_inv - szi, t0x, t0y, t0z);
-                pair_term_f64((double)fj.x - (double)fi.x, (double)fj.y - (double)fi.y, (double)fj.z - (double)fi.z,
-                              t1x, t1y, t1z);
-                qx += __double2ll_rn((t0x - t1x) * grid);
-                qy += __double2ll_rn((t0y - t1y) * grid);
-                qz += __double2ll_rn((t0z - t1z) * grid);
-            }
-            break;
-        }
-        int found = 0;
-        for (int dz = 0; dz < 2; ++dz)
-            for (int dy = 0; dy < 2; ++dy)
-                for (int dx = 0; dx < 2; ++dx) {
-                    const int cx_ = lx + dx, cy_ = ly + dy, cz_ = lz + dz;
-                    const unsigned long long hw = head[cp_bucket(cx_, cy_, cz_, mask)];
-                    if ((unsigned)(hw >> 32) != epoch) continue;
-                    int j = (int)(unsigned)hw;
-                    for (int guard = 0; j >= 0 && j < n_live && guard < n_live; ++guard, j = next[j]) {
-                        if (j == i) continue;
-                        const float4 fj = fpos[j];
-                        if (cp_cell(fj.x, hinv) != cx_ || cp_cell(fj.y, hinv) != cy_ || cp_cell(fj.z, hinv) != cz_)
-                            continue;  // another cell sharing the bucket
-                        double xj, yj, zj;
-                        pos(j, xj, yj, zj);
-                        const double ex = xj * ls_inv - sxi, ey = yj * ls_inv - syi, ez = zj * ls_inv - szi;
-                        if (!(ex * ex + ey * ey + ez * ez < dc2)) continue;
-                        double t0x, t0y, t0z, t1x, t1y, t1z;
-                        pair_term_f64(ex, ey, ez, t0x, t0y, t0z);
-                        pair_term_f64((double)fj.x - (double)fi.x, (double)fj.y - (double)fi.y,
-                                      (double)fj.z - (double)fi.z, t1x, t1y, t1z);
-                        if (pass == 0) {
-                            big = fmax(big, fmax(fabs(t0x - t1x), fmax(fabs(t0y - t1y), fabs(t0z - t1z))));
-                            if (found < CP_KEEP) keep[found] = j;
-                            ++found;
-                        } else {
-                            qx += __double2ll_rn((t0x - t1x) * grid);
-                            qy += __double2ll_rn((t0y - t1y) * grid);
-                            qz += __double2ll_rn((t0z - t1z) * grid);
-                        }
-                    }
+                const double ex = (xj - xi) * ls_inv, ey = (yj - yi) * ls_inv, ez = (zj - zi) * ls_inv;
+                if (!(ex * ex + ey * ey + ez * ez < dc2)) continue;
+                if (n == CP_KEEP) {
+                    // keep the CP_KEEP smallest j; the rest wait for the next round
+                    int m = 0;
+                    for (int k = 1; k < CP_KEEP; ++k) m = kj[k] > kj[m] ? k : m;
+                    over = 1;
+                    if (j > kj[m]) continue;
+                    close_pair_term(fi, fj, ex, ey, ez, kt[m]);
+                    kj[m] = j;
+                    continue;
                 }
-        if (pass == 0) nclose = found;
+                close_pair_term(fi, fj, ex, ey, ez, kt[n]);
+                kj[n++] = j;
+            }
+        }
+        // add this round's pairs in ascending j
+        for (int a = 0; a < n; ++a) {
+            int m = a;
+            for (int k = a + 1; k < n; ++k) m = kj[k] < kj[m] ? k : m;
+            const int tj = kj[a];
+            const float3 tt = kt[a];
+            kj[a] = kj[m];
+            kt[a] = kt[m];
+            kj[m] = tj;
+            kt[m] = tt;
+            cx += (double)kt[a].x;
+            cy += (double)kt[a].y;
+            cz += (double)kt[a].z;
+        }
+        if (!over) break;
+        last = kj[n - 1];
     }
-    if (nclose == 0 || !(big > 0.0)) {
-        cx = cy = cz = 0.0;
-        return;
-    }
-    cx = (double)qx / grid;
-    cy = (double)qy / grid;
-    cz = (double)qz / grid;
 }
 
 // ------------------------------------------------ fixed-point pair sums
@@ -557,7 +603,7 @@ __device__ __forceinline__ void push_scan_body(const Phys& P, const Bufs& B, int
             B.rem[r] = rm;
             if (!flux) {  // 1:1 replacement: the removed ion's thread samples its successor
                 Inj in;
-                sample_injection(P, C->next_id + (unsigned long long)r, sn, in);
+                injection_for(P, B, C, C->next_id, r, sn, in);
                 if (P.flags & OD_F_FP32_STATE) {
                     in.x = rnd32(in.x), in.y = rnd32(in.y), in.z = rnd32(in.z);
                     in.vx = rnd32(in.vx), in.vy = rnd32(in.vy), in.vz = rnd32(in.vz);
@@ -597,7 +643,7 @@ __device__ __forceinline__ void push_scan_body(const Phys& P, const Bufs& B, int
         int face;
         if (flux) {
             Inj in;
-            sample_injection(P, C->next_id + (unsigned long long)r, sn, in);
+            injection_for(P, B, C, C->next_id, r, sn, in);
             if (P.flags & OD_F_FP32_STATE) {
                 in.x = rnd32(in.x), in.y = rnd32(in.y), in.z = rnd32(in.z);
                 in.vx = rnd32(in.vx), in.vy = rnd32(in.vy), in.vz = rnd32(in.vz);
@@ -641,6 +687,7 @@ __device__ __forceinline__ void push_scan_body(const Phys& P, const Bufs& B, int
         C->tile_counter = 0u;
         C->done_counter = 0u;
         C->cp_epoch = cp_ep;
+        C->ahead_req_sn = (long long)sn + 1;
     }
 }
 
@@ -788,13 +835,14 @@ __device__ __forceinline__ void kick_body(const Phys& P, const Bufs& B, const Fo
             const unsigned long long id = B.id[buf][i];
             const uint4 w = philox(P, id, sn, ST_COLL);
             if ((unsigned long long)w.x < P.Tcoll) {
-                const uint4 wv = philox(P, id, sn, ST_COLL_VEL);
-                double n0, n1, n2, n3;
-                box_muller(wv.x, wv.y, n0, n1);
-                box_muller(wv.z, wv.w, n2, n3);
-                vx = P.sig_n * n0;
-                vy = P.sig_n * n1;
-                vz = P.sig_n * n2;
+                if (mode == 0 && B.coll_v) {
+                    // drawn beside the pair forces (same stream of random numbers)
+                    vx = __ldcg(B.coll_v + i);
+                    vy = __ldcg(B.coll_v + cap + i);
+                    vz = __ldcg(B.coll_v + 2 * cap + i);
+                } else {
+                    collision_velocity(P, id, sn, vx, vy, vz);
+                }
                 coll = 1;
             }
             if (P.flags & OD_F_FP32_STATE) vx = rnd32(vx), vy = rnd32(vy), vz = rnd32(vz);
@@ -866,18 +914,41 @@ constexpr int DUST_BT = 256;
 __device__ __forceinline__ void dust_body(const Phys& P, const Bufs& B, int nb, int mode)
 {
     __shared__ double s_S[MAXD][3];
+    __shared__ double s_pm[MAXD][3];
     __shared__ double s_rec[MAXD][REC];
     Ctrl* C = B.ctrl;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // deterministic reduction of the kick kernel's per-block grain sums: warp w of the nw
-    // in the CTA (8 alone, 4 inside a batch) takes components w, w + nw, ...; lanes
-    // stride the blocks, then a fixed shuffle tree (the same order for any nw)
-    for (int pc = warp; pc < P.D * 3; pc += (int)(blockDim.x >> 5)) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+    const int m_removed = mode == 0 ? C->removed_total : 0;
+    // deterministic reduction of the kick's per-block grain sums: warp w of the nw in the
+    // CTA takes components w, w + nw, ...; lanes stride the blocks, then a fixed shuffle
+    // tree (the same order for any nw)
+    for (int pc = warp; pc < P.D * 3; pc += nw) {
         const int k = pc / 3, c = pc % 3;
         double s = 0.0;
         for (int b = lane; b < nb; b += 32) s += B.dpart[((long long)b * MAXD + k) * 3 + c];
         s = warp_sum(s);
         if (lane == 0) s_S[k][c] = s;
+    }
+    // Eq. 3: momentum of the ions each grain absorbed this step (the removed-ion records in
+    // rank order: lanes stride them, then the fixed shuffle tree)
+    for (int k = warp; k < P.D; k += nw) {
+        double px = 0.0, py = 0.0, pz = 0.0;
+        for (int r = lane; r < m_removed; r += 32) {
+            const Rem rm = B.rem[r];
+            if (rm.cls == k) {
+                px += rm.vx;
+                py += rm.vy;
+                pz += rm.vz;
+            }
+        }
+        px = warp_sum(px);
+        py = warp_sum(py);
+        pz = warp_sum(pz);
+        if (lane == 0) {
+            s_pm[k][0] = P.m * px;
+            s_pm[k][1] = P.m * py;
+            s_pm[k][2] = P.m * pz;
+        }
     }
     __syncthreads();
     const int k = threadIdx.x;
@@ -900,21 +971,10 @@ __device__ __forceinline__ void dust_body(const Phys& P, const Bufs& B, int nb, 
                 fdd[1] += cc * dy;
                 fdd[2] += cc * dz;
             }
-            // Eq. 3: momentum of the ions absorbed this step, summed in index order
-            const int m = C->removed_total;
-            double pm[3] = {0.0, 0.0, 0.0};
-            for (int r = 0; r < m; ++r) {
-                const Rem rm = B.rem[r];
-                if (rm.cls == k) {
-                    pm[0] += P.m * rm.vx;
-                    pm[1] += P.m * rm.vy;
-                    pm[2] += P.m * rm.vz;
-                }
-            }
             for (int j = 0; j < 3; ++j) {
                 s_rec[k][1 + j] = fo[j];
                 s_rec[k][4 + j] = fdd[j];
-                s_rec[k][7 + j] = pm[j] / P.dt;
+                s_rec[k][7 + j] = s_pm[k][j] / P.dt;
             }
             s_rec[k][10] = 0.0;
             s_rec[k][11] = 0.0;
@@ -925,6 +985,7 @@ __device__ __forceinline__ void dust_body(const Phys& P, const Bufs& B, int nb, 
     if (mode != 0) return;
     const long long step = C->step;
     const long long sn = step + 1;
+    const long long scap = C->series_cap;
     if (k < P.D) {
         double Q = C->Q[k];
         if (P.charge_model == OD_Q_CONSISTENT) {
@@ -937,7 +998,7 @@ __device__ __forceinline__ void dust_body(const Phys& P, const Bufs& B, int nb, 
             C->Q[k] = Q;
         }
         s_rec[k][0] = Q;
-        if (step < C->series_cap) {
+        if (step < scap) {
             double* o = C->series + (step * MAXD + k) * REC;
             for (int j = 0; j < REC; ++j) o[j] = s_rec[k][j];
         }

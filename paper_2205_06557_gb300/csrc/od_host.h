@@ -22,6 +22,9 @@ struct od_handle {
     bool batch_member = false;  // stepped only through its batch (od_batch_step)
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    cudaStream_t aux = nullptr;   // next step's injection samples beside the pair forces
+    cudaStream_t aux2 = nullptr;  // this step's collision velocities beside the pair forces
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join2 = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     bool graph_ok = false;

@@ -22,6 +22,7 @@ constexpr int ERR_PLACE = 8;
 constexpr int ERR_RANGE = 32;   // a pair partial sum beyond the fixed-point range (ions nearly coincide)
 constexpr long long SPIN_LIMIT = 1ll << 22;  // ~4 s of polling with the 1 us back-off
 constexpr int VTAB_K = 4096;                  // intervals of the tabulated inverse flux CDFs
+constexpr int INJ_AHEAD = 256;                // injection samples computed one step ahead
 
 // Philox streams (fourth counter word): the same layout on host and device.
 enum : uint32_t {
@@ -42,6 +43,8 @@ struct Ctrl {
     int err;                      // ERR_* bits
     unsigned tile_counter;        // dynamic tile ids of the scan kernel
     unsigned done_counter;        // finished tiles of the scan kernel
+    unsigned kick_done;           // finished blocks of the kick (the last one runs the grain tail)
+    unsigned kick_pad;
     int removed_total;            // ions removed in the current step
     int ev_step[EV];              // this step's event counts
     int n_cur;                    // ions alive (N; varies with the flux injection rule)
@@ -51,7 +54,10 @@ struct Ctrl {
     long long wcount;             // records in the window
     long long counters[OD_NCOUNT];
     unsigned cp_epoch;            // close-pair cell lists: epoch of the last complete build (never 0)
-    unsigned cp_pad;
+    int ahead_n;                  // injection samples computed ahead: ids ahead_base + r, r < ahead_n,
+    unsigned long long ahead_base;  // for step ahead_sn (0: none), in Bufs::inj_ahead
+    long long ahead_sn;
+    long long ahead_req_sn;       // the step the next samples are for (set by the scan's last tile)
     double* series;               // [cap][MAXD][REC]
     int* evseries;                // [cap][EV]
     long long series_cap;
@@ -129,6 +135,9 @@ struct Bufs {
     unsigned long long* tile_status;
     Inj* inj;
     Rem* rem;
+    Inj* inj_ahead;  // [INJ_AHEAD] injection samples of the next step, computed during this one
+    double* coll_v;  // [3][cap] neutral velocities of this step's colliding ions, computed beside the
+                     // pair forces (null: the kick draws them)
     double* dpart; // grain partial sums [nb][MAXD][3]
     Ctrl* ctrl;
     long long cap;
@@ -194,11 +203,14 @@ int launch_push_scan(const Phys& P, const Bufs& B, cudaStream_t s);
 int launch_forces(const Phys& P, const Bufs& B, const ForceArgs& F, int variant, cudaStream_t s);
 int launch_kick(const Phys& P, const Bufs& B, const ForceArgs& F, int mode, cudaStream_t s);
 int launch_cp_bump(const Bufs& B, cudaStream_t s);  // advance the close-pair list epoch
+// the next step's first INJ_AHEAD injection samples (run beside the pair forces)
+int launch_inject_ahead(const Phys& P, const Bufs& B, cudaStream_t s);
+// this step's collision velocities (Bufs::coll_v), beside the pair forces
+int launch_collide_ahead(const Phys& P, const Bufs& B, cudaStream_t s);
 // OML floating charge of every grain into Ctrl::Q (nq Gauss-Legendre nodes glx, glw on [-1, 1])
 int launch_oml_charge(const Phys& P, const Bufs& B, double n_inf, double m_i, double Z, double T_e, int nq,
                       const double* glx, const double* glw, cudaStream_t s);
 int launch_forces_f64(const Phys& P, const Bufs& B, int after_push, cudaStream_t s);
-int launch_dust(const Phys& P, const Bufs& B, int mode, cudaStream_t s);
 int launch_stats(const Phys& P, const Bufs& B, double* mean_se, cudaStream_t s);
 // kind 0: [n][3] -> [3][cap] doubles; 1: [3][cap] -> [n][3]; 2: float4 -> [n][3] doubles;
 // 3: [n][3] doubles -> float4

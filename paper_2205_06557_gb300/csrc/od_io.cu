@@ -251,6 +251,8 @@ int od_load(const char* path, void* cuda_stream, od_handle** out)
     c.series = h->d_series;
     c.evseries = h->d_evseries;
     c.series_cap = h->series_cap;
+    c.ahead_n = 0;  // no injection samples computed ahead in this handle yet
+    c.ahead_sn = 0;
     if (cudaMemcpyAsync(h->B.ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
         return done(fail(h, OD_ECUDA, "checkpoint upload failed"));
     // the pair kernel that produced the saved state, so that the continuation is exact

@@ -6,8 +6,9 @@
 //                compaction into the other state buffer, and 1:1 re-injection (App. B)
 //   k_forces     all-pairs Yukawa ion-ion forces in FP32 (persistent, balanced tiles)
 //   k_kick       grain Coulomb force, E_out (App. A) and E_ext on ions, second half kick,
-//                Andersen collisions, and the grain-side Yukawa sums of Eq. 1 (FP64)
-//   k_dust       grain tail: Eq. 1-4 terms, charge update, records, time averages
+//                Andersen collisions, and the grain-side Yukawa sums of Eq. 1 (FP64); its
+//                last block runs the grain tail: Eq. 1-4 terms, charge update, records,
+//                time averages
 // Every kernel reads the step number from device memory, so a captured graph of one
 // step replays without the host.
 #include <algorithm>
@@ -65,6 +66,63 @@ __global__ void k_init_ions(Phys P, Bufs B, double ls_inv)
     B.fpos[i] = scaled(P, x, y, z, ls_inv);
 }
 
+// The next step's first INJ_AHEAD injection samples (ids next_id + r, step ahead_req_sn,
+// both set by this step's scan), launched on a second stream beside the pair forces; the
+// next scan uses them where the tag matches.  The tag is written after the samples.
+__global__ void __launch_bounds__(INJ_AHEAD) k_inject_ahead(Phys P, Bufs B)
+{
+    Ctrl* C = B.ctrl;
+    const long long sn = C->ahead_req_sn;
+    const unsigned long long base = C->next_id;
+    if (sn <= 0) return;
+    Inj o;
+    sample_injection(P, base + threadIdx.x, (uint32_t)sn, o);
+    o.pad = 0;
+    B.inj_ahead[threadIdx.x] = o;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        C->ahead_n = INJ_AHEAD;
+        C->ahead_base = base;
+        C->ahead_sn = sn;
+    }
+}
+
+// This step's collision velocities, beside the pair forces: the ions' order and ids are
+// final after the scan, and a collision depends only on (seed, id, step), so the kick
+// finds the FP64 Box-Muller draws of its colliding ions ready.
+__global__ void k_collide_ahead(Phys P, Bufs B)
+{
+    const Ctrl* C = B.ctrl;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= C->n_cur) return;
+    const long long step = C->step;
+    const int buf = (int)((step + 1) & 1);
+    const uint32_t sn = (uint32_t)(step + 1);
+    const unsigned long long id = B.id[buf][i];
+    const uint4 w = philox(P, id, sn, ST_COLL);
+    if ((unsigned long long)w.x >= P.Tcoll) return;
+    double vx, vy, vz;
+    collision_velocity(P, id, sn, vx, vy, vz);
+    B.coll_v[i] = vx;
+    B.coll_v[B.cap + i] = vy;
+    B.coll_v[2 * B.cap + i] = vz;
+}
+
+int launch_collide_ahead(const Phys& P, const Bufs& B, cudaStream_t s)
+{
+    if (P.N == 0 || !B.coll_v) return 0;
+    k_collide_ahead<<<(P.N + 255) / 256, 256, 0, s>>>(P, B);
+    return (int)cudaGetLastError();
+}
+
+int launch_inject_ahead(const Phys& P, const Bufs& B, cudaStream_t s)
+{
+    if (P.N == 0) return 0;
+    k_inject_ahead<<<1, INJ_AHEAD, 0, s>>>(P, B);
+    return (int)cudaGetLastError();
+}
+
 // publishes the close-pair lists built by k_fpos (their epoch becomes the current one)
 __global__ void k_cp_bump(Ctrl* C) { C->cp_epoch = cp_next_epoch(C->cp_epoch); }
 
@@ -94,13 +152,23 @@ __global__ void __launch_bounds__(BT) k_push_scan(Phys P, Bufs B, int n_tiles, d
     push_scan_body<BT>(P, B, n_tiles, ls_inv, -1);
 }
 
+// The kick, then the grain tail in the last block to finish (the grain update reads every
+// block's sums; one launch fewer per step than a separate tail kernel)
 template <int BT>
 __global__ void __launch_bounds__(BT) k_kick(Phys P, Bufs B, ForceArgs F, int mode)
 {
+    __shared__ int s_last;
     kick_body<BT>(P, B, F, mode, blockIdx.x);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&B.ctrl->kick_done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (threadIdx.x == 0) B.ctrl->kick_done = 0u;
+    dust_body(P, B, (int)gridDim.x, mode);
 }
 
-__global__ void __launch_bounds__(DUST_BT) k_dust(Phys P, Bufs B, int nb, int mode) { dust_body(P, B, nb, mode); }
 
 __global__ void k_stats(Phys P, Bufs B, double* out)
 {
@@ -311,8 +379,8 @@ int launch_pad(const Phys& P, const Bufs& B, cudaStream_t s) { return launch_fpo
 int launch_push_scan(const Phys& P, const Bufs& B, cudaStream_t s)
 {
     if (P.N == 0) return 0;
-    const int n_tiles = (P.N + PUSH_BT - 1) / PUSH_BT;
     const double ls_inv = 1.4426950408889634 * P.lam_inv;
+    const int n_tiles = (P.N + PUSH_BT - 1) / PUSH_BT;
     k_push_scan<PUSH_BT><<<n_tiles, PUSH_BT, 0, s>>>(P, B, n_tiles, ls_inv);
     return ck(cudaGetLastError());
 }
@@ -448,12 +516,6 @@ int launch_kick(const Phys& P, const Bufs& B, const ForceArgs& F, int mode, cuda
     return ck(cudaGetLastError());
 }
 
-int launch_dust(const Phys& P, const Bufs& B, int mode, cudaStream_t s)
-{
-    const int nb = P.N == 0 ? 0 : (P.N + KICK_BT - 1) / KICK_BT;
-    k_dust<<<1, DUST_BT, 0, s>>>(P, B, nb, mode);
-    return ck(cudaGetLastError());
-}
 
 // host interface layouts: the ABI's interleaved [n][3] arrays <-> the device's [3][cap]
 // structure of arrays (and the float4 accelerations), converted on the device so that a

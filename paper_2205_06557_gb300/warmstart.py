@@ -58,6 +58,28 @@ def study_run(seed, steps, n_inf=4e13, R=2e-4, H=4e-4):
     return p
 
 
+def chain_run(seed, steps, n_inf=1e15, R=1.5e-4, H=1.2e-3):
+    """A dust-chain run (the shape of the paper's chain tests): 2-8 grains of radius
+    U(10, 20) um on the axis of an elongated cylinder, centred, spaced U(1, 3) ion Debye
+    lengths apart along the flow; Mach U(0.3, 2), collision frequency from {1e5, 1e6, 5e6}
+    /s, consistent charging from the OML charges (by default ~85,000 ions at 1e15 m^-3)."""
+    rng = np.random.default_rng(70_000 + seed)
+    p = W.plasma_ar(mach=float(rng.uniform(0.3, 2.0)), nu=float(rng.choice([1e5, 1e6, 5e6])))
+    p["n_inf"] = n_inf
+    lam_di = math.sqrt(EPS0 * KB * p["T_i"] / (n_inf * QE * QE))
+    nd = int(rng.integers(2, 9))
+    radii = rng.uniform(1e-5, 2e-5, nd)
+    gaps = np.maximum(rng.uniform(1.0, 3.0, nd - 1) * lam_di, 1.2 * (radii[1:] + radii[:-1]))
+    zs = np.concatenate([[0.0], np.cumsum(gaps)])
+    zs -= zs.mean()
+    dust = [dict(x=0.0, y=0.0, z=float(z), a=float(a), q0=0.0) for z, a in zip(zs, radii)]
+    p.update(R=R, H=H, dt=5e-10, n_ions=0, seed=seed, charge_model="consistent", dust=dust,
+             avg_start=steps // 2 + 1)
+    for g in p["dust"]:
+        g["q0"] = od_oml_charge(p, g["a"])
+    return p
+
+
 def _psi_scale(p, a):
     return 4 * math.pi * EPS0 * a * KB * p["T_e"] / QE  # charge per unit dimensionless potential
 

@@ -31,6 +31,24 @@ def test_features_and_targets_are_consistent():
     assert all(g["q0"] < 0 for g in p["dust"])
 
 
+def test_chain_runs_are_valid_inputs():
+    """held-out dust-chain runs: 2-8 grains on the axis, inside the domain, not overlapping,
+    features in the ranges the network was trained on"""
+    from paper_2205_06557_gb300 import warmstart as ws
+
+    for seed in range(6):
+        p = ws.chain_run(seed, 1000)
+        D = len(p["dust"])
+        assert 2 <= D <= 8
+        zs = np.array([g["z"] for g in p["dust"]])
+        a = np.array([g["a"] for g in p["dust"]])
+        assert np.all(np.diff(zs) > a[1:] + a[:-1])
+        assert np.all(np.abs(zs) + a < 0.5 * p["H"])
+        x, m = ws.features(p)
+        assert m.sum() == D and np.all(np.abs(x[:D, 3:6]) <= 1.0)
+        assert all(g["q0"] < 0 for g in p["dust"])
+
+
 def test_steps_to_converge():
     from paper_2205_06557_gb300.warmstart import steps_to_converge
 
