@@ -40,7 +40,7 @@ UNIT = "pairs/s"
 SFU_CLK_PER_PAIR = 1 / 16 + 1 / 32
 PAIRS_PER_CLK_SM = {0: min(128 / 14, 1 / SFU_CLK_PER_PAIR), 1: min(128 / 8.5, 2 / SFU_CLK_PER_PAIR),
                     2: min(128 / 8.5, 2 / SFU_CLK_PER_PAIR)}
-KERNEL_SOURCES = ("od_pairs.cuh", "od_device.cuh", "od_internal.h", "od_kernels.cu")
+KERNEL_SOURCES = ("od_pairs.cuh", "od_pairmath.cuh", "od_internal.h")
 
 
 def kernel_sources_hash():

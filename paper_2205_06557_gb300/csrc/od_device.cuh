@@ -4,23 +4,11 @@
 #pragma once
 
 #include "od_internal.h"
+#include "od_pairmath.cuh"
 
 namespace od {
 
 // ------------------------------------------------------------------ helpers
-__device__ __forceinline__ float rsqrt_approx(float x)
-{
-    float r;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
-
-__device__ __forceinline__ float ex2_approx(float x)
-{
-    float r;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
 
 __device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v)
 {
@@ -366,28 +354,6 @@ __device__ void close_pair_corr(const unsigned long long* __restrict__ head, con
     }
 }
 
-// ------------------------------------------------ fixed-point pair sums
-// A symmetric unit adds its FP32 partial sum v of ion q as round(v 2^K) to a 64-bit
-// integer (red.global.add): integer addition is associative, so the total does not depend
-// on which CTA evaluates which unit or in what order.  |v 2^K| must stay below 2^60
-// (K is set per run from the expected term sum, ~2^30 below it); otherwise ERR_RANGE.
-__device__ __forceinline__ void fixed_add(long long* a, float v, float qscale, int* err)
-{
-    float t = v * qscale;
-    if (!(fabsf(t) < 1.152921504606847e18f)) {
-        atomicOr(err, t != t ? ERR_NAN : ERR_RANGE);
-        t = 0.f;
-    }
-    atomicAdd((unsigned long long*)a, (unsigned long long)__float2ll_rn(t));
-}
-
-__device__ __forceinline__ void fixed_add3(long long* acc, long long ld, long long q, float vx, float vy, float vz,
-                                           float qscale, int* err)
-{
-    fixed_add(acc + q, vx, qscale, err);
-    fixed_add(acc + ld + q, vy, qscale, err);
-    fixed_add(acc + 2 * ld + q, vz, qscale, err);
-}
 
 // Number of superions injected in step sn under the flux rule: Poisson with mean lam,
 // split into chunks of at most 64, each drawn by inversion (summing e^-l l^x / x! in
@@ -713,6 +679,7 @@ template <int BT>
 __device__ __forceinline__ void kick_body(const Phys& P, const Bufs& B, const ForceArgs& F, int mode, int blk)
 {
     __shared__ double s_red[BT / 32][3];
+    __shared__ double s_Q[MAXD];
     Ctrl* C = B.ctrl;
     const long long step = C->step;
     const int buf = mode == 0 ? (int)((step + 1) & 1) : (int)(step & 1);
@@ -721,23 +688,42 @@ __device__ __forceinline__ void kick_body(const Phys& P, const Bufs& B, const Fo
     const bool live = i < C->n_cur;
     const long long cap = B.cap;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    double x = 0, y = 0, z = 0;
-    int coll = 0;
+    const bool sym_sums = F.sym && !(P.flags & OD_F_NO_IONION);
+    // every load that does not depend on another is issued first (one memory round trip):
+    // position, velocity, id, the fixed-point pair sums, the grain charges
+    double x = 0, y = 0, z = 0, vx = 0, vy = 0, vz = 0;
+    unsigned long long id = 0;
+    long long qa = 0, qb = 0, qc = 0;
+    long long* A = nullptr;
     if (live) {
         const double* X = B.x[buf];
         x = X[i];
         y = X[cap + i];
         z = X[2 * cap + i];
+        if (mode == 0) {
+            const double* V = B.v[buf];
+            vx = V[i];
+            vy = V[cap + i];
+            vz = V[2 * cap + i];
+            id = B.id[buf][i];
+        }
+        if (sym_sums) {
+            // symmetric kernels (all pairs or the cutoff's listed tile pairs): the fixed-point
+            // sum at the ion's position in the pair kernel's order (cleared below)
+            A = F.psum + (F.cut ? F.rank[i] : i);
+            qa = A[0];
+            qb = A[F.psum_ld];
+            qc = A[2 * F.psum_ld];
+        }
+    }
+    if ((int)threadIdx.x < P.D) s_Q[threadIdx.x] = C->Q[threadIdx.x];
+    __syncthreads();
+    int coll = 0;
+    if (live) {
         float ax = 0.f, ay = 0.f, az = 0.f;
         if (!(P.flags & OD_F_NO_IONION)) {
             double px = 0.0, py = 0.0, pz = 0.0;  // pair sum in scaled units
             if (F.sym) {
-                // symmetric kernels (all pairs or the cutoff's listed tile pairs): the
-                // fixed-point sum at the ion's position in the pair kernel's order, read and
-                // cleared for the next evaluation
-                const long long q = F.cut ? F.rank[i] : i;
-                long long* A = F.psum + q;
-                const long long qa = A[0], qb = A[F.psum_ld], qc = A[2 * F.psum_ld];
                 A[0] = 0;
                 A[F.psum_ld] = 0;
                 A[2 * F.psum_ld] = 0;
@@ -808,7 +794,7 @@ __device__ __forceinline__ void kick_body(const Phys& P, const Bufs& B, const Fo
             const float dx = (float)(x - P.gx[k]), dy = (float)(y - P.gy[k]), dz = (float)(z - P.gz[k]);
             const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
             const float ri = rsqrt_approx(r2);
-            const float c = (float)(P.kdi * C->Q[k]) * (ri * ri * ri);
+            const float c = (float)(P.kdi * s_Q[k]) * (ri * ri * ri);
             ax = fmaf(c, dx, ax);
             ay = fmaf(c, dy, ay);
             az = fmaf(c, dz, az);
@@ -826,13 +812,11 @@ __device__ __forceinline__ void kick_body(const Phys& P, const Bufs& B, const Fo
         B.acc[i] = a;
         if (mode == 0) {
             double* V = B.v[buf];
-            double vx = V[i], vy = V[cap + i], vz = V[2 * cap + i];
             const double h = 0.5 * P.dt;
             vx += h * (double)a.x;
             vy += h * (double)a.y;
             vz += h * (double)a.z;
             // Andersen collision with the neutrals: integer threshold on a Philox word
-            const unsigned long long id = B.id[buf][i];
             const uint4 w = philox(P, id, sn, ST_COLL);
             if ((unsigned long long)w.x < P.Tcoll) {
                 if (mode == 0 && B.coll_v) {

@@ -112,6 +112,7 @@ def generate(n_runs, steps, seed0=0, batch_runs=256, stream=None, **domain):
     for c0 in range(0, n_runs, batch_runs):
         ps = [study_run(seed0 + s, steps, **domain) for s in range(c0, min(n_runs, c0 + batch_runs))]
         b = Batch(ps, stream=stream)
+        b.tune(reps=1)  # the batch's pair plan (ordered chunks or symmetric tile pairs)
         b.step(steps)
         for p, run in zip(ps, b.runs):
             mean, _ = run.dust_terms()
@@ -215,6 +216,7 @@ def evaluate(net, norm, plist, steps, tol=0.01, stream=None, details=False):
             r["avg_start"] = steps - steps // 4 + 1
             runs.append(r)
     b = Batch(runs, stream=stream)
+    b.tune(reps=1)  # the batch's pair plan (ordered chunks or symmetric tile pairs)
     import time
 
     t0 = time.perf_counter()
