@@ -900,26 +900,50 @@ __device__ __forceinline__ void dust_body(const Phys& P, const Bufs& B, int nb, 
     __shared__ double s_S[MAXD][3];
     __shared__ double s_pm[MAXD][3];
     __shared__ double s_rec[MAXD][REC];
+    __shared__ double s_Qd[MAXD];
     Ctrl* C = B.ctrl;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+    const int k = threadIdx.x, j = threadIdx.x;
+    // the control block's values this tail needs are loaded first, together (one memory
+    // round trip): step, removal count, series pointers, each grain's charge, event count
+    // and window sums, each event counter
+    const long long step = C->step;
+    const long long scap = C->series_cap;
     const int m_removed = mode == 0 ? C->removed_total : 0;
+    double* const series = C->series;
+    int* const evseries = C->evseries;
+    double Qk = 0.0, wk[REC];
+    int evk = 0;
+    if (k < P.D) {
+        Qk = C->Q[k];
+        evk = C->ev_step[k];
+        if (mode == 0)
+#pragma unroll
+            for (int t = 0; t < REC; ++t) wk[t] = C->wsum[k][t];
+    }
+    int evj = 0;
+    long long cntj = 0;
+    if (mode == 0 && j < EV) {
+        evj = C->ev_step[j];
+        cntj = C->counters[j];
+    }
     // deterministic reduction of the kick's per-block grain sums: warp w of the nw in the
     // CTA takes components w, w + nw, ...; lanes stride the blocks, then a fixed shuffle
     // tree (the same order for any nw)
     for (int pc = warp; pc < P.D * 3; pc += nw) {
-        const int k = pc / 3, c = pc % 3;
-        double s = 0.0;
-        for (int b = lane; b < nb; b += 32) s += B.dpart[((long long)b * MAXD + k) * 3 + c];
-        s = warp_sum(s);
-        if (lane == 0) s_S[k][c] = s;
+        const int kk = pc / 3, c = pc % 3;
+        double sum = 0.0;
+        for (int b = lane; b < nb; b += 32) sum += B.dpart[((long long)b * MAXD + kk) * 3 + c];
+        sum = warp_sum(sum);
+        if (lane == 0) s_S[kk][c] = sum;
     }
     // Eq. 3: momentum of the ions each grain absorbed this step (the removed-ion records in
     // rank order: lanes stride them, then the fixed shuffle tree)
-    for (int k = warp; k < P.D; k += nw) {
+    for (int kk = warp; kk < P.D; kk += nw) {
         double px = 0.0, py = 0.0, pz = 0.0;
         for (int r = lane; r < m_removed; r += 32) {
             const Rem rm = B.rem[r];
-            if (rm.cls == k) {
+            if (rm.cls == kk) {
                 px += rm.vx;
                 py += rm.vy;
                 pz += rm.vz;
@@ -929,20 +953,20 @@ __device__ __forceinline__ void dust_body(const Phys& P, const Bufs& B, int nb, 
         py = warp_sum(py);
         pz = warp_sum(pz);
         if (lane == 0) {
-            s_pm[k][0] = P.m * px;
-            s_pm[k][1] = P.m * py;
-            s_pm[k][2] = P.m * pz;
+            s_pm[kk][0] = P.m * px;
+            s_pm[kk][1] = P.m * py;
+            s_pm[kk][2] = P.m * pz;
         }
     }
+    if (k < P.D) s_Qd[k] = Qk;
     __syncthreads();
-    const int k = threadIdx.x;
     if (k < P.D) {
-        const double Q = C->Q[k];
+        const double Q = Qk;
         double ex = 0.0, ey = 0.0, ez = 0.0;
         if (P.eout) eout_field(P, P.gx[k], P.gy[k], P.gz[k], ex, ey, ez);
         const double c = P.korb * Q;
         const double fo[3] = {c * s_S[k][0] + ex * Q, c * s_S[k][1] + ey * Q, c * s_S[k][2] + ez * Q};
-        for (int j = 0; j < 3; ++j) C->f_orbit[k][j] = fo[j];
+        for (int t = 0; t < 3; ++t) C->f_orbit[k][t] = fo[t];
         if (mode == 0) {
             // Eq. 2: Coulomb force of the other grains
             double fdd[3] = {0.0, 0.0, 0.0};
@@ -950,52 +974,47 @@ __device__ __forceinline__ void dust_body(const Phys& P, const Bufs& B, int nb, 
                 if (p == k) continue;
                 const double dx = P.gx[k] - P.gx[p], dy = P.gy[k] - P.gy[p], dz = P.gz[k] - P.gz[p];
                 const double d = sqrt(dx * dx + dy * dy + dz * dz);
-                const double cc = P.inv4pieps0 * Q * C->Q[p] / (d * d * d);
+                const double cc = P.inv4pieps0 * Q * s_Qd[p] / (d * d * d);
                 fdd[0] += cc * dx;
                 fdd[1] += cc * dy;
                 fdd[2] += cc * dz;
             }
-            for (int j = 0; j < 3; ++j) {
-                s_rec[k][1 + j] = fo[j];
-                s_rec[k][4 + j] = fdd[j];
-                s_rec[k][7 + j] = s_pm[k][j] / P.dt;
+            for (int t = 0; t < 3; ++t) {
+                s_rec[k][1 + t] = fo[t];
+                s_rec[k][4 + t] = fdd[t];
+                s_rec[k][7 + t] = s_pm[k][t] / P.dt;
             }
             s_rec[k][10] = 0.0;
             s_rec[k][11] = 0.0;
             s_rec[k][12] = Q * P.E;  // Eq. 4
+            // the charge update (explicit: the forces above used the charge before it)
+            double Qn = Q;
+            if (P.charge_model == OD_Q_CONSISTENT) {
+                // absorbed superions plus the OML electron flux at the isolated-sphere potential
+                const double a = P.ga[k];
+                const double xe = Q * P.inv4pieps0 / a * P.e_over_kTe;
+                const double fac = xe <= 0.0 ? exp(xe) : 1.0 + xe;
+                const double flux = 4.0 * 3.141592653589793 * a * a * P.Ie0 * fac;
+                Qn = Q + P.q * (double)evk - 1.602176634e-19 * flux * P.dt;
+                C->Q[k] = Qn;
+            }
+            s_rec[k][0] = Qn;
+            if (step < scap) {
+                double* o = series + (step * MAXD + k) * REC;
+                for (int t = 0; t < REC; ++t) o[t] = s_rec[k][t];
+            }
+            if (step + 1 >= P.avg_start)
+                for (int t = 0; t < REC; ++t) C->wsum[k][t] = wk[t] + s_rec[k][t];
         }
     }
-    __syncthreads();
     if (mode != 0) return;
-    const long long step = C->step;
-    const long long sn = step + 1;
-    const long long scap = C->series_cap;
-    if (k < P.D) {
-        double Q = C->Q[k];
-        if (P.charge_model == OD_Q_CONSISTENT) {
-            // absorbed superions plus the OML electron flux at the isolated-sphere potential
-            const double a = P.ga[k];
-            const double xe = Q * P.inv4pieps0 / a * P.e_over_kTe;
-            const double fac = xe <= 0.0 ? exp(xe) : 1.0 + xe;
-            const double flux = 4.0 * 3.141592653589793 * a * a * P.Ie0 * fac;
-            Q = Q + P.q * (double)C->ev_step[k] - 1.602176634e-19 * flux * P.dt;
-            C->Q[k] = Q;
-        }
-        s_rec[k][0] = Q;
-        if (step < scap) {
-            double* o = C->series + (step * MAXD + k) * REC;
-            for (int j = 0; j < REC; ++j) o[j] = s_rec[k][j];
-        }
-        if (sn >= P.avg_start)
-            for (int j = 0; j < REC; ++j) C->wsum[k][j] += s_rec[k][j];
-    }
+    // one thread per event counter: record, accumulate, reset for the next step (the grain
+    // threads above read their own counts before this block reaches here: the barrier)
     __syncthreads();
-    // one thread per event counter: record, accumulate, reset for the next step
-    const int j = threadIdx.x;
+    const long long sn = step + 1;
     if (j < EV) {
-        const int e = C->ev_step[j];
-        if (step < C->series_cap) C->evseries[step * EV + j] = e;
-        C->counters[j] += e;
+        if (step < scap) evseries[step * EV + j] = evj;
+        C->counters[j] = cntj + evj;
         C->ev_step[j] = 0;
     } else if (j == 32) {
         C->counters[13] = sn;
