@@ -338,6 +338,7 @@ void derive(const od_params* p, Phys& P, od_handle* h)
     const double Js = 2.0 * kPI * p->R * p->H * P.sig / std::sqrt(2.0 * kPI);
     const double J = Jb + Jt + Js;
     P.inj_lambda = p->n_inf / p->weight * J * p->dt;
+    P.inj_ahead_flux = (int)std::min((double)INJ_AHEAD, std::ceil(P.inj_lambda + 6.0 * std::sqrt(P.inj_lambda)) + 32.0);
     P.Tb = prob_threshold(Jb / J);
     P.Tbt = prob_threshold((Jb + Jt) / J);
     const double pc = -std::expm1(-p->nu_in * p->dt);
@@ -762,6 +763,8 @@ void free_all(od_handle* h)
     free_cut(h);
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
     if (h->graph) cudaGraphDestroy(h->graph);
+    if (h->gexec_k) cudaGraphExecDestroy(h->gexec_k);
+    if (h->graph_k) cudaGraphDestroy(h->graph_k);
     for (auto& e : h->ev)
         if (e) cudaEventDestroy(e);
     for (auto& e : h->pev)
@@ -833,10 +836,11 @@ int create_impl(const od_params* p, od_handle* h)
     B.psum_ld = h->npad_cap;
     OD_CK(h, cudaMalloc(&B.psum, sizeof(long long) * 3 * h->npad_cap));
     OD_CK(h, cudaMemsetAsync(B.psum, 0, sizeof(long long) * 3 * h->npad_cap, h->stream));
-    // (eight buckets per ion up to 2^18 ions: the walks then meet few ions of other cells;
-    // two per ion above, which keeps the grid near the L2's size)
+    // (32 buckets per ion up to 2^16 ions and 8 up to 2^18: the walks then meet few ions
+    // of other cells; two per ion above, which keeps the grid near the L2's size)
     unsigned long long nbk = 1024;
-    const unsigned long long want = (h->cap <= (1 << 18) ? 8ull : 2ull) * (unsigned long long)h->cap;
+    const unsigned long long per_ion = h->cap <= (1 << 16) ? 32ull : h->cap <= (1 << 18) ? 8ull : 2ull;
+    const unsigned long long want = per_ion * (unsigned long long)h->cap;
     while (nbk < want) nbk <<= 1;
     h->P.cp_mask = (unsigned)(nbk - 1);
     OD_CK(h, cudaMalloc(&B.cp_head, sizeof(unsigned long long) * nbk));
@@ -873,6 +877,7 @@ int create_impl(const od_params* p, od_handle* h)
     c0.cp_epoch = 1;  // bucket words start at epoch 0, which no build uses
     for (int k = 0; k < p->n_dust; ++k) c0.Q[k] = p->charge_model == OD_Q_OML ? 0.0 : p->dust[k].q0;
     OD_CK(h, cudaMemcpyAsync(B.ctrl, &c0, sizeof(Ctrl), cudaMemcpyHostToDevice, h->stream));
+    OD_LK(h, launch_grain_eout(h->P, B, h->stream));
     if (p->charge_model == OD_Q_OML && p->n_dust > 0) {
         // the grains' OML floating charges, solved on the device
         std::vector<double> gx, gw;
@@ -952,22 +957,43 @@ int od_step(od_handle* h, int64_t n)
     int rc = ensure_series(h, h->host_step + n);
     if (rc) return rc;
     const bool direct = h->profiling || (h->P.flags & OD_F_NO_GRAPH);
-    if (!direct && !h->graph_ok) {
-        if (h->gexec) cudaGraphExecDestroy(h->gexec);
-        if (h->graph) cudaGraphDestroy(h->graph);
-        h->gexec = nullptr;
-        h->graph = nullptr;
+    // one step per graph, and STEP_GRAPH_K steps per graph for long calls: a small run's
+    // step is a few tens of microseconds, of which a graph launch per step would be a
+    // good part
+    auto capture = [h](int steps, cudaGraph_t* graph, cudaGraphExec_t* exec) -> int {
+        if (*exec) cudaGraphExecDestroy(*exec);
+        if (*graph) cudaGraphDestroy(*graph);
+        *exec = nullptr;
+        *graph = nullptr;
         OD_CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-        int lrc = launch_step(h);
+        int lrc = 0;
+        for (int k = 0; k < steps && !lrc; ++k) lrc = launch_step(h);
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamEndCapture(h->stream, &g);
-        if (lrc) return lrc;
+        if (lrc) {
+            if (g) cudaGraphDestroy(g);
+            return lrc;
+        }
         if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
-        h->graph = g;
-        OD_CK(h, cudaGraphInstantiate(&h->gexec, g, 0));
+        *graph = g;
+        OD_CK(h, cudaGraphInstantiate(exec, g, 0));
+        return OD_OK;
+    };
+    if (!direct && !h->graph_ok) {
+        h->graph_k_ok = false;
+        if ((rc = capture(1, &h->graph, &h->gexec))) return rc;
         h->graph_ok = true;
     }
+    if (!direct && n >= STEP_GRAPH_K && !h->graph_k_ok) {
+        if ((rc = capture(STEP_GRAPH_K, &h->graph_k, &h->gexec_k))) return rc;
+        h->graph_k_ok = true;
+    }
     for (int64_t s = 0; s < n; ++s) {
+        if (!direct && n - s >= STEP_GRAPH_K) {
+            OD_CK(h, cudaGraphLaunch(h->gexec_k, h->stream));
+            s += STEP_GRAPH_K - 1;
+            continue;
+        }
         if (direct) {
             if (h->profiling) {
                 // events around each kernel, read PROF_RING steps at a time, so that the

@@ -291,66 +291,77 @@ __device__ void close_pair_corr(const unsigned long long* __restrict__ head, con
     const int lx = c0x - (ux - (float)c0x < 0.5f), ly = c0y - (uy - (float)c0y < 0.5f),
               lz = c0z - (uz - (float)c0z < 0.5f);
     const float dc2_f = (float)(1.01 * dc2);
-    int kj[CP_KEEP];
-    float3 kt[CP_KEEP];
-    int n = 0, over = 0;
-    int last = -1;  // with more than CP_KEEP close pairs: the pairs up to j = last are summed
-    cx = cy = cz = 0.0;
     // the eight bucket words are loaded at once (one memory round trip, not eight)
     unsigned long long hws[8];
 #pragma unroll
     for (int c = 0; c < 8; ++c) hws[c] = head[cp_bucket(lx + (c & 1), ly + ((c >> 1) & 1), lz + (c >> 2), mask)];
+    cx = cy = cz = 0.0;
+    int last = -1;  // with more than CP_KEEP candidates: the pairs up to j = last are summed
     for (int round = 0; round < n_live; ++round) {
-        n = 0;
-        over = 0;
-#pragma unroll 1
-        for (int c = 0; c < 8; ++c) {
-            const int cx_ = lx + (c & 1), cy_ = ly + ((c >> 1) & 1), cz_ = lz + (c >> 2);
-            const unsigned long long hw = hws[c];
-            if ((unsigned)(hw >> 32) != epoch) continue;
-            int j = (int)(unsigned)hw;
-            for (int guard = 0; j >= 0 && j < n_live && guard < n_live; ++guard, j = next[j]) {
-                if (j == i || j <= last) continue;
-                const float4 fj = fpos[j];
-                if (cp_cell(fj.x, hinv) != cx_ || cp_cell(fj.y, hinv) != cy_ || cp_cell(fj.z, hinv) != cz_)
-                    continue;  // another cell sharing the bucket
-                // FP32 pre-test on the rounded separation (a 1% margin in d^2 covers its rounding)
-                const float gx = fj.x - fi.x, gy = fj.y - fi.y, gz = fj.z - fi.z;
-                if (fmaf(gx, gx, fmaf(gy, gy, gz * gz)) > dc2_f) continue;
-                double xj, yj, zj;
-                pos(j, xj, yj, zj);
-                const double ex = (xj - xi) * ls_inv, ey = (yj - yi) * ls_inv, ez = (zj - zi) * ls_inv;
-                if (!(ex * ex + ey * ey + ez * ez < dc2)) continue;
-                if (n == CP_KEEP) {
-                    // keep the CP_KEEP smallest j; the rest wait for the next round
-                    int m = 0;
-                    for (int k = 1; k < CP_KEEP; ++k) m = kj[k] > kj[m] ? k : m;
-                    over = 1;
-                    if (j > kj[m]) continue;
-                    close_pair_term(fi, fj, ex, ey, ez, kt[m]);
-                    kj[m] = j;
-                    continue;
+        // the eight lists are walked side by side: each step loads the next entry (position
+        // and link) of every list at once, so a walk costs one memory round trip per list
+        // level, not one per entry.  Candidates: another ion of the same cell, j > last,
+        // within the correction distance by the FP32 pre-test (a 1% margin in d^2 covers
+        // its rounding); the CP_KEEP smallest j are kept.
+        int jc[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) jc[c] = (unsigned)(hws[c] >> 32) == epoch ? (int)(unsigned)hws[c] : -1;
+        int cand[CP_KEEP];
+        int nc = 0, over = 0;
+        for (int level = 0; level < n_live; ++level) {
+            float4 fj[8];
+            int nx[8];
+            bool any = false;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                nx[c] = -1;
+                if (jc[c] >= 0 && jc[c] < n_live) {
+                    fj[c] = fpos[jc[c]];
+                    nx[c] = next[jc[c]];
+                    any = true;
                 }
-                close_pair_term(fi, fj, ex, ey, ez, kt[n]);
-                kj[n++] = j;
+            }
+            if (!any) break;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const int j = jc[c];
+                jc[c] = nx[c];
+                if (!(j >= 0 && j < n_live) || j == i || j <= last) continue;
+                if (cp_cell(fj[c].x, hinv) != lx + (c & 1) || cp_cell(fj[c].y, hinv) != ly + ((c >> 1) & 1) ||
+                    cp_cell(fj[c].z, hinv) != lz + (c >> 2))
+                    continue;  // another cell sharing the bucket
+                const float gx = fj[c].x - fi.x, gy = fj[c].y - fi.y, gz = fj[c].z - fi.z;
+                if (fmaf(gx, gx, fmaf(gy, gy, gz * gz)) > dc2_f) continue;
+                if (nc < CP_KEEP) {
+                    cand[nc++] = j;
+                } else {
+                    // keep the CP_KEEP smallest j; the rest wait for the next round
+                    over = 1;
+                    int m = 0;
+                    for (int k = 1; k < CP_KEEP; ++k) m = cand[k] > cand[m] ? k : m;
+                    if (j < cand[m]) cand[m] = j;
+                }
             }
         }
-        // add this round's pairs in ascending j
-        for (int a = 0; a < n; ++a) {
+        // this round's candidates in ascending j: the FP64 distance test, then the term
+        for (int a = 0; a < nc; ++a) {
             int m = a;
-            for (int k = a + 1; k < n; ++k) m = kj[k] < kj[m] ? k : m;
-            const int tj = kj[a];
-            const float3 tt = kt[a];
-            kj[a] = kj[m];
-            kt[a] = kt[m];
-            kj[m] = tj;
-            kt[m] = tt;
-            cx += (double)kt[a].x;
-            cy += (double)kt[a].y;
-            cz += (double)kt[a].z;
+            for (int k = a + 1; k < nc; ++k) m = cand[k] < cand[m] ? k : m;
+            const int j = cand[m];
+            cand[m] = cand[a];
+            cand[a] = j;
+            double xj, yj, zj;
+            pos(j, xj, yj, zj);
+            const double ex = (xj - xi) * ls_inv, ey = (yj - yi) * ls_inv, ez = (zj - zi) * ls_inv;
+            if (!(ex * ex + ey * ey + ez * ez < dc2)) continue;
+            float3 t;
+            close_pair_term(fi, fpos[j], ex, ey, ez, t);
+            cx += (double)t.x;
+            cy += (double)t.y;
+            cz += (double)t.z;
         }
         if (!over) break;
-        last = kj[n - 1];
+        last = cand[nc - 1];
     }
 }
 
@@ -654,6 +665,9 @@ __device__ __forceinline__ void push_scan_body(const Phys& P, const Bufs& B, int
         C->done_counter = 0u;
         C->cp_epoch = cp_ep;
         C->ahead_req_sn = (long long)sn + 1;
+        // the next step's injections: the flux rule's Poisson mean plus six deviations, or
+        // (one per removed ion) twice this step's removals; the scan draws any beyond
+        C->ahead_want = flux ? P.inj_ahead_flux : min(2 * m + 32, INJ_AHEAD);
     }
 }
 
@@ -912,11 +926,14 @@ __device__ __forceinline__ void dust_body(const Phys& P, const Bufs& B, int nb, 
     const int m_removed = mode == 0 ? C->removed_total : 0;
     double* const series = C->series;
     int* const evseries = C->evseries;
-    double Qk = 0.0, wk[REC];
+    double Qk = 0.0, wk[REC], egx = 0.0, egy = 0.0, egz = 0.0;
     int evk = 0;
     if (k < P.D) {
         Qk = C->Q[k];
         evk = C->ev_step[k];
+        egx = C->eg[k][0];
+        egy = C->eg[k][1];
+        egz = C->eg[k][2];
         if (mode == 0)
 #pragma unroll
             for (int t = 0; t < REC; ++t) wk[t] = C->wsum[k][t];
@@ -938,11 +955,14 @@ __device__ __forceinline__ void dust_body(const Phys& P, const Bufs& B, int nb, 
         if (lane == 0) s_S[kk][c] = sum;
     }
     // Eq. 3: momentum of the ions each grain absorbed this step (the removed-ion records in
-    // rank order: lanes stride them, then the fixed shuffle tree)
+    // rank order: lanes stride them, then the fixed shuffle tree; the first 32 records are
+    // loaded beside the count, which is read in the same round trip)
+    Rem rm0 = {0.0, 0.0, 0.0, -2, 0};
+    if (lane < B.cap) rm0 = B.rem[lane];
     for (int kk = warp; kk < P.D; kk += nw) {
         double px = 0.0, py = 0.0, pz = 0.0;
         for (int r = lane; r < m_removed; r += 32) {
-            const Rem rm = B.rem[r];
+            const Rem rm = r == lane ? rm0 : B.rem[r];
             if (rm.cls == kk) {
                 px += rm.vx;
                 py += rm.vy;
@@ -962,8 +982,7 @@ __device__ __forceinline__ void dust_body(const Phys& P, const Bufs& B, int nb, 
     __syncthreads();
     if (k < P.D) {
         const double Q = Qk;
-        double ex = 0.0, ey = 0.0, ez = 0.0;
-        if (P.eout) eout_field(P, P.gx[k], P.gy[k], P.gz[k], ex, ey, ez);
+        const double ex = egx, ey = egy, ez = egz;
         const double c = P.korb * Q;
         const double fo[3] = {c * s_S[k][0] + ex * Q, c * s_S[k][1] + ey * Q, c * s_S[k][2] + ez * Q};
         for (int t = 0; t < 3; ++t) C->f_orbit[k][t] = fo[t];

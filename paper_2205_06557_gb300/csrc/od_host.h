@@ -10,6 +10,7 @@
 #include "od_internal.h"
 
 constexpr int PROF_RING = 64;  // steps per read of the profiling events
+constexpr int STEP_GRAPH_K = 16;  // steps in the long step graph
 
 struct od_handle {
     od::Phys P{};
@@ -27,7 +28,10 @@ struct od_handle {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join2 = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
-    bool graph_ok = false;
+    bool graph_ok = false;  // false: both step graphs are recaptured before the next step
+    cudaGraph_t graph_k = nullptr;  // STEP_GRAPH_K steps in one graph (long od_step calls)
+    cudaGraphExec_t gexec_k = nullptr;
+    bool graph_k_ok = false;
     long long cap = 0;       // ion capacity
     long long npad_cap = 0;  // fpos capacity
     long long part_cap = 0;  // partial-sum capacity (float4)

@@ -22,7 +22,7 @@ constexpr int ERR_PLACE = 8;
 constexpr int ERR_RANGE = 32;   // a pair partial sum beyond the fixed-point range (ions nearly coincide)
 constexpr long long SPIN_LIMIT = 1ll << 22;  // ~4 s of polling with the 1 us back-off
 constexpr int VTAB_K = 4096;                  // intervals of the tabulated inverse flux CDFs
-constexpr int INJ_AHEAD = 256;                // injection samples computed one step ahead
+constexpr int INJ_AHEAD = 2048;               // injection samples computed one step ahead (at most)
 
 // Philox streams (fourth counter word): the same layout on host and device.
 enum : uint32_t {
@@ -44,12 +44,13 @@ struct Ctrl {
     unsigned tile_counter;        // dynamic tile ids of the scan kernel
     unsigned done_counter;        // finished tiles of the scan kernel
     unsigned kick_done;           // finished blocks of the kick (the last one runs the grain tail)
-    unsigned kick_pad;
+    unsigned inj_done;            // finished blocks of the injection sampler (the last one tags)
     int removed_total;            // ions removed in the current step
     int ev_step[EV];              // this step's event counts
     int n_cur;                    // ions alive (N; varies with the flux injection rule)
     double Q[MAXD];               // grain charges
     double f_orbit[MAXD][3];      // Eq. 1 force at the last force evaluation
+    double eg[MAXD][3];           // E_out at each grain's centre (App. A; set at creation)
     double wsum[MAXD][REC];       // window sums of the records
     long long wcount;             // records in the window
     long long counters[OD_NCOUNT];
@@ -58,6 +59,8 @@ struct Ctrl {
     unsigned long long ahead_base;  // for step ahead_sn (0: none), in Bufs::inj_ahead
     long long ahead_sn;
     long long ahead_req_sn;       // the step the next samples are for (set by the scan's last tile)
+    int ahead_want;               // how many to draw (the scan's estimate of the next step's need)
+    int ahead_pad;
     double* series;               // [cap][MAXD][REC]
     int* evseries;                // [cap][EV]
     long long series_cap;
@@ -118,6 +121,8 @@ struct Phys {
     float cp_hinv;
     double cp_dc2;
     double ls_inv;     // log2(e) / lambda_De in FP64
+    int inj_ahead_flux;  // samples drawn ahead per step under the flux rule: lambda + 6 sqrt(lambda) + 32
+    int inj_pad;
 };
 
 // Device buffers. Ion state is double-buffered (compaction writes the other copy).
@@ -208,6 +213,8 @@ int launch_inject_ahead(const Phys& P, const Bufs& B, cudaStream_t s);
 // this step's collision velocities (Bufs::coll_v), beside the pair forces
 int launch_collide_ahead(const Phys& P, const Bufs& B, cudaStream_t s);
 // OML floating charge of every grain into Ctrl::Q (nq Gauss-Legendre nodes glx, glw on [-1, 1])
+// E_out at the grain centres into Ctrl::eg (once, at creation)
+int launch_grain_eout(const Phys& P, const Bufs& B, cudaStream_t s);
 int launch_oml_charge(const Phys& P, const Bufs& B, double n_inf, double m_i, double Z, double T_e, int nq,
                       const double* glx, const double* glw, cudaStream_t s);
 int launch_forces_f64(const Phys& P, const Bufs& B, int after_push, cudaStream_t s);

@@ -66,23 +66,37 @@ __global__ void k_init_ions(Phys P, Bufs B, double ls_inv)
     B.fpos[i] = scaled(P, x, y, z, ls_inv);
 }
 
-// The next step's first INJ_AHEAD injection samples (ids next_id + r, step ahead_req_sn,
-// both set by this step's scan), launched on a second stream beside the pair forces; the
-// next scan uses them where the tag matches.  The tag is written after the samples.
-__global__ void __launch_bounds__(INJ_AHEAD) k_inject_ahead(Phys P, Bufs B)
+// The next step's first injection samples (ids next_id + r, r < ahead_want <= INJ_AHEAD,
+// for step ahead_req_sn, all set by this step's scan), launched on a second stream beside
+// the pair forces; the next scan uses them where the tag matches and draws the rest
+// itself.  The tag is written after the samples.
+constexpr int INJ_BT = 32;  // one warp per block: FP64 is slow on this GPU, so the draws
+                            // are spread over as many SMs as there are warps of them
+
+__global__ void __launch_bounds__(INJ_BT) k_inject_ahead(Phys P, Bufs B)
 {
+    __shared__ int s_last;
     Ctrl* C = B.ctrl;
     const long long sn = C->ahead_req_sn;
     const unsigned long long base = C->next_id;
-    if (sn <= 0) return;
-    Inj o;
-    sample_injection(P, base + threadIdx.x, (uint32_t)sn, o);
-    o.pad = 0;
-    B.inj_ahead[threadIdx.x] = o;
+    const int want = min(C->ahead_want, (int)(gridDim.x * INJ_BT));
+    const int r = blockIdx.x * INJ_BT + threadIdx.x;
+    if (sn > 0 && r < want) {
+        Inj o;
+        sample_injection(P, base + (unsigned long long)r, (uint32_t)sn, o);
+        o.pad = 0;
+        B.inj_ahead[r] = o;
+    }
+    // the last block to finish tags the samples (after every block's have been written)
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) {
-        C->ahead_n = INJ_AHEAD;
+    if (threadIdx.x == 0) s_last = atomicAdd(&C->inj_done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last || threadIdx.x != 0) return;
+    __threadfence();
+    C->inj_done = 0u;
+    if (sn > 0) {
+        C->ahead_n = want;
         C->ahead_base = base;
         C->ahead_sn = sn;
     }
@@ -119,7 +133,24 @@ int launch_collide_ahead(const Phys& P, const Bufs& B, cudaStream_t s)
 int launch_inject_ahead(const Phys& P, const Bufs& B, cudaStream_t s)
 {
     if (P.N == 0) return 0;
-    k_inject_ahead<<<1, INJ_AHEAD, 0, s>>>(P, B);
+    k_inject_ahead<<<INJ_AHEAD / INJ_BT, INJ_BT, 0, s>>>(P, B);
+    return (int)cudaGetLastError();
+}
+
+__global__ void k_grain_eout(Phys P, Ctrl* C)
+{
+    const int k = threadIdx.x;
+    if (k >= P.D) return;
+    double ex = 0.0, ey = 0.0, ez = 0.0;
+    if (P.eout) eout_field(P, P.gx[k], P.gy[k], P.gz[k], ex, ey, ez);
+    C->eg[k][0] = ex;
+    C->eg[k][1] = ey;
+    C->eg[k][2] = ez;
+}
+
+int launch_grain_eout(const Phys& P, const Bufs& B, cudaStream_t s)
+{
+    k_grain_eout<<<1, MAXD, 0, s>>>(P, B.ctrl);
     return (int)cudaGetLastError();
 }
 
