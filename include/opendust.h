@@ -323,6 +323,29 @@ int od_sur_train_step(od_sur* s, const float* x, const float* mask, const float*
                       double* loss);
 const char* od_sur_last_error(const od_sur* s);
 
+/* Matrix-product engine of the network's forward and backward passes:
+ *   OD_GEMM_TCGEN05 (default): the fifth-generation tensor cores (tcgen05.mma, M = 128
+ *     tiles, FP32 accumulators in tensor memory, operands staged in shared memory);
+ *   OD_GEMM_MMA_SYNC: warp-level mma.sync m16n8k16 tiles, kept as an independent
+ *     cross-check of the first.
+ * Both take BF16 operands and accumulate in FP32; their results differ only in the order
+ * of the FP32 additions.  Returns OD_EINVAL for another value. */
+#define OD_GEMM_TCGEN05 0
+#define OD_GEMM_MMA_SYNC 1
+int od_sur_set_gemm(od_sur* s, int engine);
+
+/* One product with either engine on device buffers (the network's products, exposed for
+ * tests): C[M][N] = A[M][K] B[N][K]^T (+ bias[N]) (max(., 0) if relu), FP32 C and,
+ * if Cb is not NULL, its BF16 rounding.  A, B: BF16 (bit pattern in uint16), row-major,
+ * K contiguous; bias: FP32 or NULL; all device pointers, 16-byte aligned.  Sizes:
+ * K and N multiples of 16 for both engines, M a multiple of 16 for OD_GEMM_MMA_SYNC
+ * (any M >= 1 for OD_GEMM_TCGEN05).  err: device int the caller zeroes; a tensor-core
+ * wait that gives up (never expected) ORs 2 into it, the call still returns.  Asynchronous
+ * on `stream` (cudaStream_t, NULL = legacy default stream).  OD_EINVAL for bad sizes or
+ * engine, OD_ECUDA for a launch failure. */
+int od_gemm_bf16(const uint16_t* A, const uint16_t* B, const float* bias, float* C, uint16_t* Cb, int M, int N,
+                 int K, int relu, int engine, int* err, void* stream);
+
 /* Failure-detection self-test (no counterpart in the paper): runs one push/scan kernel in
  * which the first scan tile withholds its prefix, so the look-back wait of the next
  * tile finds no inclusive prefix and gives up after `polls` polls instead of its usual

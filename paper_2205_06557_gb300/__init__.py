@@ -101,6 +101,10 @@ def lib():
         L.od_last_error.restype = ctypes.c_char_p
         L.od_pair_accel_static.argtypes = [vp, i64, ctypes.c_double, ctypes.c_double, vp, vp]
         L.od_pair_accel_static.restype = ctypes.c_int
+        L.od_sur_set_gemm.argtypes = [vp, i32]
+        L.od_sur_set_gemm.restype = ctypes.c_int
+        L.od_gemm_bf16.argtypes = [vp, vp, vp, vp, vp, i32, i32, i32, i32, i32, vp, vp]
+        L.od_gemm_bf16.restype = ctypes.c_int
         L.od_tune.argtypes = [vp, ctypes.c_int, vp, vp, vp, vp]
         L.od_set_force_config.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         L.od_get_force_config.argtypes = [vp, vp, vp, vp, vp]
@@ -434,6 +438,18 @@ def tune_cached(h, key, reps=3, path=None):
 STATIC_MAX_IONS = 32768
 
 
+GEMM_TCGEN05, GEMM_MMA_SYNC = 0, 1
+
+
+def od_gemm_bf16(a_dev, b_dev, bias_dev, c_dev, cb_dev, M, N, K, relu, engine, err_dev, stream=None):
+    """C = A B^T (+ bias) (relu) on device buffers (addresses as ints; bias_dev and cb_dev
+    may be 0); err_dev: a zeroed device int32 (see od_gemm_bf16 in opendust.h)."""
+    vp = ctypes.c_void_p
+    return _check(lib().od_gemm_bf16(vp(a_dev), vp(b_dev), vp(bias_dev or None), vp(c_dev), vp(cb_dev or None),
+                                     int(M), int(N), int(K), int(relu), int(engine), vp(err_dev),
+                                     vp(stream) if stream else None))
+
+
 def od_pair_accel_static(x_dev, n, lambda_De, k, a_dev, stream=None):
     """Pair accelerations without device allocation. x_dev, a_dev are device
     addresses (ints) of [n][3] FP64 positions and [n][3] FP32 accelerations."""
@@ -599,6 +615,10 @@ class Surrogate:
         loss = ctypes.c_double()
         self._chk(lib().od_sur_gradients(self.h, _ptr(x), _ptr(mask), _ptr(t), x.shape[0], ctypes.byref(loss), _ptr(g)))
         return loss.value, g
+
+    def set_gemm(self, engine):
+        """GEMM_TCGEN05 (default) or GEMM_MMA_SYNC for every matrix product."""
+        self._chk(lib().od_sur_set_gemm(self.h, int(engine)))
 
     def train_step(self, x, mask, t, lr):
         x, mask, t = self._f32(x), self._f32(mask), self._f32(t)

@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libopendust.so")
-SOURCES = ["od_kernels.cu", "od_api.cu", "od_batch.cu", "od_sur.cu", "od_peaks.cu", "od_cut.cu", "od_config.cu", "od_io.cu", "od_batch_api.cu"]
+SOURCES = ["od_kernels.cu", "od_api.cu", "od_batch.cu", "od_sur.cu", "od_gemm_tc.cu", "od_peaks.cu", "od_cut.cu", "od_config.cu", "od_io.cu", "od_batch_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

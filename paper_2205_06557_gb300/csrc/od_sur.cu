@@ -10,7 +10,8 @@
 //   h4_k = relu(W4 h3_k + b4)           256
 //   y_k  = W5 h4_k + b5                 4 outputs (padded to 16)
 // Weights are kept in FP32 (master copy for Adam) and used as BF16 in every matrix
-// product (BF16 inputs, FP32 accumulation, tensor-core mma.sync m16n8k16 tiles);
+// product (BF16 inputs, FP32 accumulation: tcgen05.mma tiles by default, od_gemm_tc.cu,
+// or warp-level mma.sync m16n8k16 tiles, k_gemm_nt below);
 // activations are rounded to BF16 where they enter a product.  The loss is the mean
 // squared error over present grains and the four outputs.
 #include <cuda_bf16.h>
@@ -230,6 +231,8 @@ struct od_sur {
     float *h1, *h2, *c, *h3, *h4, *y, *dy, *dx, *dx3, *da, *rowl, *mask, *tgt, *xin;
     cudaStream_t stream = nullptr;
     long long adam_t = 0;
+    int engine = OD_GEMM_TCGEN05;
+    int* d_err = nullptr;  // tensor-core wait timeouts (bit 1)
     std::string err;
 };
 
@@ -252,12 +255,42 @@ int sfail(od_sur* s, int code, const std::string& msg)
 
 inline int blocks(long long n, int bt = 256) { return (int)((n + bt - 1) / bt); }
 
+}  // namespace
+
+namespace od {
+int launch_gemm_tc(const __nv_bfloat16* A, const __nv_bfloat16* B, const float* bias, float* C, __nv_bfloat16* Cb,
+                   int M, int N, int K, int relu, int* err, cudaStream_t s);
+
+int gemm_bf16(const __nv_bfloat16* A, const __nv_bfloat16* B, const float* bias, float* C, __nv_bfloat16* Cb, int M,
+              int N, int K, int relu, int engine, int* err, cudaStream_t stream)
+{
+    if (engine == OD_GEMM_TCGEN05) return launch_gemm_tc(A, B, bias, C, Cb, M, N, K, relu, err, stream);
+    const long long warps = (long long)(M / 16) * (N / 16);
+    k_gemm_nt<<<blocks(warps * 32, 128), 128, 0, stream>>>(A, B, bias, C, Cb, M, N, K, relu);
+    return (int)cudaGetLastError();
+}
+}  // namespace od
+
+namespace {
+
 int gemm(od_sur* s, const __nv_bfloat16* A, const __nv_bfloat16* B, const float* bias, float* C, __nv_bfloat16* Cb, int M,
          int N, int K, int relu)
 {
-    const long long warps = (long long)(M / 16) * (N / 16);
-    k_gemm_nt<<<blocks(warps * 32, 128), 128, 0, s->stream>>>(A, B, bias, C, Cb, M, N, K, relu);
-    return cudaGetLastError() == cudaSuccess ? OD_OK : sfail(s, OD_ECUDA, "gemm launch failed");
+    const int e = gemm_bf16(A, B, bias, C, Cb, M, N, K, relu, s->engine, s->d_err, s->stream);
+    return e == 0 ? OD_OK : sfail(s, OD_ECUDA, std::string("gemm launch failed: ") + cudaGetErrorString((cudaError_t)e));
+}
+
+// tensor-core waits that gave up since the last check (read after a synchronisation)
+int check_engine(od_sur* s)
+{
+    int e = 0;
+    SCK(s, cudaMemcpyAsync(&e, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+    SCK(s, cudaStreamSynchronize(s->stream));
+    if (e) {
+        SCK(s, cudaMemsetAsync(s->d_err, 0, sizeof(int), s->stream));
+        return sfail(s, OD_ETIMEOUT, "a tensor-core product's wait gave up");
+    }
+    return OD_OK;
 }
 
 void free_sur(od_sur* s)
@@ -269,6 +302,7 @@ void free_sur(od_sur* s)
     void* bufs[] = {s->x0b, s->h1b, s->h2b, s->x3b, s->h3b, s->h4b, s->dyb, s->dzb, s->tA, s->tB, s->h1, s->h2,
                     s->c, s->h3, s->h4, s->y, s->dy, s->dx, s->dx3, s->da, s->rowl, s->mask, s->tgt, s->xin};
     for (void* p : bufs) cudaFree(p);
+    cudaFree(s->d_err);
 }
 
 // refresh the BF16 copies of every layer from the FP32 masters
@@ -448,6 +482,8 @@ int od_sur_create(int max_batch, uint64_t seed, void* stream, od_sur** out)
     mb((void**)&s->mask, 4 * M);
     mb((void**)&s->tgt, 4 * M * OUTR);
     mb((void**)&s->xin, 4 * M * K0);
+    mb((void**)&s->d_err, sizeof(int));
+    if (ok) ok = cudaMemsetAsync(s->d_err, 0, sizeof(int), s->stream) == cudaSuccess;
     if (!ok || refresh_bf16(s) != OD_OK || cudaStreamSynchronize(s->stream) != cudaSuccess) {
         g_sur_error = "surrogate allocation failed";
         free_sur(s);
@@ -519,7 +555,7 @@ int od_sur_forward(od_sur* s, const float* x, const float* mask, int Bn, float* 
     if ((rc = forward(s, Bp))) return rc;
     std::vector<float> yy((size_t)M * OUTP);
     SCK(s, cudaMemcpyAsync(yy.data(), s->y, sizeof(float) * yy.size(), cudaMemcpyDeviceToHost, s->stream));
-    SCK(s, cudaStreamSynchronize(s->stream));
+    if ((rc = check_engine(s))) return rc;
     for (int r = 0; r < Bn * G; ++r)
         for (int o = 0; o < OUTR; ++o) y[(size_t)r * OUTR + o] = yy[(size_t)r * OUTP + o];
     return OD_OK;
@@ -537,6 +573,7 @@ int od_sur_gradients(od_sur* s, const float* x, const float* mask, const float* 
     int rc = upload_batch(s, xs.data(), ms.data(), ts.data(), Bp);
     if (rc) return rc;
     if ((rc = loss_and_grad(s, Bp, ms.data(), loss))) return rc;
+    if (loss && (rc = check_engine(s))) return rc;
     if (grads) {
         size_t off = 0;
         for (auto& l : s->L) {
@@ -545,7 +582,7 @@ int od_sur_gradients(od_sur* s, const float* x, const float* mask, const float* 
             SCK(s, cudaMemcpyAsync(grads + off, l.gb, sizeof(float) * l.out, cudaMemcpyDeviceToHost, s->stream));
             off += l.out;
         }
-        SCK(s, cudaStreamSynchronize(s->stream));
+        if ((rc = check_engine(s))) return rc;
     }
     return OD_OK;
 }
@@ -569,5 +606,22 @@ int od_sur_train_step(od_sur* s, const float* x, const float* mask, const float*
 }
 
 const char* od_sur_last_error(const od_sur* s) { return s ? s->err.c_str() : g_sur_error.c_str(); }
+
+int od_sur_set_gemm(od_sur* s, int engine)
+{
+    if (!s || (engine != OD_GEMM_TCGEN05 && engine != OD_GEMM_MMA_SYNC)) return sfail(s, OD_EINVAL, "bad engine");
+    s->engine = engine;
+    return OD_OK;
+}
+
+int od_gemm_bf16(const uint16_t* A, const uint16_t* B, const float* bias, float* C, uint16_t* Cb, int M, int N, int K,
+                 int relu, int engine, int* err, void* stream)
+{
+    if (!A || !B || !C || !err || M < 1 || N < 16 || K < 16 || N % 16 || K % 16) return OD_EINVAL;
+    if (engine != OD_GEMM_TCGEN05 && (engine != OD_GEMM_MMA_SYNC || M % 16)) return OD_EINVAL;
+    const int e = gemm_bf16((const __nv_bfloat16*)A, (const __nv_bfloat16*)B, bias, C, (__nv_bfloat16*)Cb, M, N, K,
+                            relu, engine, err, (cudaStream_t)stream);
+    return e == 0 ? OD_OK : OD_ECUDA;
+}
 
 }  // extern "C"

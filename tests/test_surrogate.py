@@ -1,7 +1,8 @@
 """The warm-start network: its FP64 CPU reference is pinned by central finite
 differences; the GPU's hand-written forward/backward (BF16 products, FP32
-accumulation) is checked against that reference with the same BF16 roundings; and a
-learning test shows the GPU training loop fits a smooth synthetic target."""
+accumulation, on either matrix-product engine) is checked against that reference with
+the same BF16 roundings; and a learning test shows the GPU training loop fits a smooth
+synthetic target."""
 import numpy as np
 import pytest
 
@@ -69,10 +70,12 @@ def test_reference_pooling_is_permutation_invariant():
 
 
 @pytest.mark.gpu
-def test_gpu_gradients_match_reference():
+@pytest.mark.parametrize("engine", ["tcgen05", "mma_sync"])
+def test_gpu_gradients_match_reference(engine):
     import paper_2205_06557_gb300 as od
 
     s = od.Surrogate(max_batch=16, seed=7)
+    s.set_gemm(od.GEMM_TCGEN05 if engine == "tcgen05" else od.GEMM_MMA_SYNC)
     p = s.get_params().astype(np.float64)
     assert p.size == N_PARAMS
     x, mask, t = _inputs(6, 11)
