@@ -113,8 +113,10 @@ int od_create(const od_params* p, od_handle** out);
 
 /* Advance n >= 0 time steps (the canonical order: half kick and drift; absorption and
  * outflow; compaction and re-injection; forces; half kick; collisions; grain update).
- * Work is queued on the run's stream; the call waits for it to read the device error
- * word: OD_ENAN, OD_ETIMEOUT or OD_ECUDA report a failure inside the steps. */
+ * Work is queued on the run's stream as replayed CUDA graphs (16 steps per graph while 16
+ * or more remain, one step per graph for the rest; captured on first use and again after a
+ * configuration change); the call waits for it to read the device error word: OD_ENAN,
+ * OD_ETIMEOUT or OD_ECUDA report a failure inside the steps. */
 int od_step(od_handle* h, int64_t n);
 
 /* Time averages over steps avg_start..current (Sec. 2 results): q[D] mean charge (C)
