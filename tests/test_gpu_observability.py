@@ -121,7 +121,8 @@ def test_ion_dumps_hold_the_exact_state(tmp_path):
 def test_kernel_times_span_more_steps_than_the_event_ring():
     """per-kernel profiling records events for every step and reads them 64 steps at a
     time: a call of 70 steps and one of 5 count 75 launches of each stage, and the
-    profiled (directly launched) steps give the same bits as graph-replayed ones"""
+    profiled (directly launched) steps give the same bits as graph-replayed ones (75 steps
+    in one call: four 16-step graphs and eleven one-step graphs), state and records"""
     p = W.tiny(steps=200)
     prof, ref = od.Run(p), od.Run(p)
     od.od_set_profiling(prof.h, 1)
@@ -133,5 +134,28 @@ def test_kernel_times_span_more_steps_than_the_event_ring():
     ref.step(75)
     for a, b in zip(prof.get_ions(), ref.get_ions()):
         assert np.array_equal(a, b)
+    for a, b in zip(prof.series(1, 75), ref.series(1, 75)):
+        assert np.array_equal(a, b)
     prof.close()
     ref.close()
+
+
+def test_step_graph_lengths_give_the_same_bits():
+    """od_step replays 16-step graphs while 16 or more steps remain and one-step graphs for
+    the rest: 40 steps as one call, as 16 + 1 + 23, and one at a time end in the same state
+    and records"""
+    p = W.tiny(steps=200)
+    runs = [od.Run(p) for _ in range(3)]
+    runs[0].step(40)
+    for k in (16, 1, 23):
+        runs[1].step(k)
+    for _ in range(40):
+        runs[2].step(1)
+    ref_state, ref_series = runs[0].get_ions(), runs[0].series(1, 40)
+    for r in runs[1:]:
+        for a, b in zip(r.get_ions(), ref_state):
+            assert np.array_equal(a, b)
+        for a, b in zip(r.series(1, 40), ref_series):
+            assert np.array_equal(a, b)
+    for r in runs:
+        r.close()
