@@ -1,26 +1,31 @@
 // BF16 matrix products of the warm-start network on the fifth-generation tensor cores:
 // C[M][N] = A[M][K] B[N][K]^T (+ bias[N]) (relu), FP32 accumulation in tensor memory.
 //
-// One CTA of 128 threads computes a 128 x NT tile of C (NT <= 256, a multiple of 16 that
-// divides N).  K is consumed in chunks of 32 (64 bytes of every row) through a ring of four
-// shared-memory stages: the CTA's threads copy chunk c + 2 in with cp.async while the tensor
-// cores multiply chunk c, so two chunks' copies are in flight behind the products.  Operands
-// sit in shared memory in the canonical K-major layout without swizzling: 8-row x 16-byte
-// core matrices, the 4 core matrices of a chunk's 8-row group side by side (128 bytes apart
-// along K), the row groups 512 bytes apart.  One elected thread issues tcgen05.mma
-// (M = 128, N = NT, K = 16, two per chunk) and commits each chunk's products to that stage's
-// mbarrier, which the copy into the stage four chunks later waits for.  The accumulator
-// lives in tensor memory (one lane per row of the tile, NT columns); the epilogue reads it
-// with tcgen05.ld (warp w: rows 32w .. 32w + 31, 16 columns at a time), adds the bias,
-// applies the relu and stages each 32 x 16 block in shared memory, so that the stores to C
-// and to its BF16 copy write 64 contiguous bytes of a row per four lanes instead of one
-// row per lane.
+// One CTA of 128 threads computes a 128 x NT tile of C (NT <= 128, a multiple of 16 that
+// divides N; two CTAs per SM; the N tiles of a row block launch next to each other).  K is
+// consumed in chunks of 64 (128 bytes of every row) through a ring of three shared-memory
+// stages filled by the tensor memory accelerator (TMA).  One thread runs the pipeline: per
+// chunk, a TMA load of the A tile (128 x 64) and of the B tile (NT x 64) into a stage, both
+// completing on the stage's "full" mbarrier by their byte count; once a chunk has landed,
+// its four tcgen05.mma (M = 128, N = NT, K = 16), committed to the stage's "empty" mbarrier,
+// which the load of the chunk three later into that stage waits for.  Two chunks' loads
+// are in flight behind the products.  The tiles arrive in the 128-byte swizzled layout (row
+// r of a tile at 128 r bytes, its 16-byte pieces permuted by r mod 8) that the shared-memory
+// descriptors name (SWIZZLE_128B, 1,024 bytes between 8-row groups, K steps of 32 bytes
+// within the swizzle span); rows past M and columns past K are zero-filled by the loads.
+// After the last chunk the four warps read the accumulator with tcgen05.ld (warp w: rows
+// 32w .. 32w + 31, 16 columns at a time), add the bias, apply the relu and stage each
+// 32 x 16 block in shared memory, so that the stores of C and of its BF16 copy write 64
+// contiguous bytes of a row per four lanes.
 //
 // Every wait on an mbarrier is bounded: a wait that runs out sets bit 1 of *err, stops
 // the CTA's further products and still frees its tensor memory before returning.
+#include <cuda.h>  // CUtensorMap and the encoder's types; the encoder itself is fetched
+                   // through the runtime's entry-point query (no link to libcuda)
 #include <cuda_bf16.h>
 
 #include <cstdint>
+#include <mutex>
 
 #include "od_internal.h"
 
@@ -29,31 +34,33 @@ namespace tc {
 
 constexpr int BT = 128;                    // threads per CTA (four warps: 128 TMEM lanes)
 constexpr int TM = 128;                    // tile rows
-constexpr int TK = 32;                     // K per chunk (64 bytes of a BF16 row)
-constexpr int STAGES = 4;                  // chunks in the shared-memory ring
-constexpr int AHEAD = 2;                   // chunks copied ahead of the one multiplied
-constexpr int NT_MAX = 256;                // widest tile (one MMA instruction's N)
-constexpr int A_BYTES = TM * TK * 2;       // 8 KB
+constexpr int TK = 64;                     // K per chunk (128 bytes of a BF16 row: one swizzle span)
+constexpr int STAGES = 3;                  // chunks in the shared-memory ring
+constexpr int NT_MAX = 128;                // widest tile
+constexpr int A_BYTES = TM * TK * 2;       // 16 KB
 constexpr int B_BYTES = NT_MAX * TK * 2;   // 16 KB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr uint32_t SBO = 8 * TK * 2;       // bytes between 8-row groups (512)
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 64;  // stages, alignment, barriers
+constexpr uint32_t SBO = 8 * TK * 2;       // bytes between 8-row groups (1,024)
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 128;  // stages, alignment, barriers
 constexpr int EPI_LD = 20;                 // staged epilogue row stride (floats; 80 B)
 constexpr long long WAIT_LIMIT = 1ll << 22;  // polls of an mbarrier before giving up
+static_assert(A_BYTES % 1024 == 0 && B_BYTES % 1024 == 0, "swizzled tiles start on 1,024-byte boundaries");
 static_assert(4 * 32 * EPI_LD * 4 <= STAGES * STAGE_BYTES, "epilogue staging fits the stages");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-// shared-memory matrix descriptor: start, leading (K-direction core-matrix) and stride
-// (8-row-group) byte offsets, descriptor version 1, no swizzle
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+// shared-memory matrix descriptor of a K-major tile in the 128-byte swizzled layout:
+// start address, leading byte offset 16 (unused for this layout), stride byte offset
+// 1,024 (8 rows of 128 bytes), descriptor version 1, layout type 2 (SWIZZLE_128B)
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr)
 {
     uint64_t d = 0;
     d |= (uint64_t)((addr >> 4) & 0x3FFFu);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-    d |= (uint64_t)1 << 46;  // version
-    return d;                // base offset 0, layout type 0 (no swizzle)
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)((SBO >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
 }
 
 // instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both K-major
@@ -92,44 +99,52 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity)
     return false;
 }
 
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool valid)
+// the A and B tiles of chunk c into stage c % STAGES, completing on that stage's full barrier
+__device__ __forceinline__ void load_chunk(const CUtensorMap* tmA, const CUtensorMap* tmB, uint8_t* smem,
+                                           uint64_t* full, int c, int m0, int n0, uint32_t bytes)
 {
-    const int n = valid ? 16 : 0;  // zero-fill when the row is outside the matrix
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(n) : "memory");
+    const int st = c % STAGES;
+    const uint32_t sa = smem_u32(smem + st * STAGE_BYTES), sb = sa + A_BYTES, bar = smem_u32(&full[st]);
+    const int k0 = c * TK;  // innermost coordinate: a multiple of 64 elements (128 bytes)
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            sa),
+        "l"((uint64_t)tmA), "r"(k0), "r"(m0), "r"(bar)
+        : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            sb),
+        "l"((uint64_t)tmB), "r"(k0), "r"(n0), "r"(bar)
+        : "memory");
 }
 
-// copy a rows x 32 BF16 chunk (rows from r0, K from k0) into the core-matrix layout:
-// thread t writes the 16 bytes at offset 16 t of the stage, i.e. row group t / 32, core
-// matrix (t / 8) % 4 along K, row t % 8 within it
-__device__ __forceinline__ void load_chunk(uint32_t dst, const __nv_bfloat16* __restrict__ src, int rows, int r0,
-                                           int nrows, int K, int k0)
-{
-    const int n16 = rows * (TK / 8);
-    for (int t = threadIdx.x; t < n16; t += BT) {
-        const int rg = t >> 5, kg = (t >> 3) & 3, r = t & 7;
-        const int row = r0 + rg * 8 + r, k = k0 + kg * 8;
-        const bool valid = row < nrows && k < K;
-        const __nv_bfloat16* p = valid ? src + (long long)row * K + k : src;
-        cp_async16(dst + 16u * (uint32_t)t, p, valid);
-    }
-}
-
-__global__ void __launch_bounds__(BT) k_gemm_tc(const __nv_bfloat16* __restrict__ A, const __nv_bfloat16* __restrict__ B,
-                                                const float* __restrict__ bias, float* __restrict__ C,
-                                                __nv_bfloat16* __restrict__ Cb, int M, int N, int K, int NT, int relu,
-                                                int* err)
+__global__ void __launch_bounds__(BT) k_gemm_tc(const __grid_constant__ CUtensorMap tmA,
+                                                const __grid_constant__ CUtensorMap tmB, const float* __restrict__ bias,
+                                                float* __restrict__ C, __nv_bfloat16* __restrict__ Cb, int M, int N,
+                                                int K, int NT, int relu, int* err)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t* bar = (uint64_t*)(smem + STAGES * STAGE_BYTES);  // one barrier per stage
-    uint32_t* tmem_slot = (uint32_t*)(bar + STAGES);
+    uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);  // loads landed, per stage
+    uint64_t* empty = full + STAGES;                             // products done reading, per stage
+    uint32_t* tmem_slot = (uint32_t*)(empty + STAGES);
+    __shared__ int s_fail;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.x * TM, n0 = blockIdx.y * NT;
-    const uint32_t ncols = NT <= 32 ? 32u : NT <= 64 ? 64u : NT <= 128 ? 128u : 256u;
+    // the N tiles of one row block are neighbours in launch order, so they run together and
+    // the second reads the A tile from L2
+    const int m0 = blockIdx.y * TM, n0 = blockIdx.x * NT;
+    const uint32_t ncols = NT <= 32 ? 32u : NT <= 64 ? 64u : 128u;
 
     if (threadIdx.x == 0) {
-        for (int st = 0; st < STAGES; ++st) mbar_init(&bar[st], 1);
+        for (int st = 0; st < STAGES; ++st) {
+            mbar_init(&full[st], 1);
+            mbar_init(&empty[st], 1);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmB) : "memory");
+        s_fail = 0;
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
@@ -142,45 +157,28 @@ __global__ void __launch_bounds__(BT) k_gemm_tc(const __nv_bfloat16* __restrict_
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
 
-    const uint32_t idesc = instr_desc(TM, NT);
-    const int nchunks = (K + TK - 1) / TK;
-    auto stage_a = [&](int c) { return smem_u32(smem + (c % STAGES) * STAGE_BYTES); };
-    auto copy = [&](int c) {
-        if (c < nchunks) {
-            load_chunk(stage_a(c), A, TM, m0, M, K, c * TK);
-            load_chunk(stage_a(c) + A_BYTES, B, NT, n0, N, K, c * TK);
-        }
-        asm volatile("cp.async.commit_group;" ::: "memory");  // (empty past the last chunk)
-    };
-    unsigned phase[STAGES] = {0u, 0u, 0u, 0u};
-    bool failed = false;
-    for (int c = 0; c < AHEAD; ++c) copy(c);
-    for (int c = 0; c < nchunks; ++c) {
-        // the stage of chunk c + AHEAD was last read by the products of chunk c + AHEAD - STAGES
-        const int cn = c + AHEAD, cold = cn - STAGES;
-        if (cn < nchunks && cold >= 0) {
-            const int st = cold % STAGES;
-            const bool ok = mbar_wait(&bar[st], phase[st]);
-            phase[st] ^= 1u;
-            if (__syncthreads_or(!ok)) {
-                failed = true;
-                break;
-            }
-        }
-        copy(cn);
-        // every group but the AHEAD newest is complete: chunk c has landed
-        asm volatile("cp.async.wait_group %0;" ::"n"(AHEAD) : "memory");
-        // make the copies visible to the tensor cores (the async proxy)
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (threadIdx.x == 0) {
+    if (threadIdx.x == 0) {
+        // the pipeline, in one thread: products of chunk c, then the load of chunk c + 2 into
+        // the stage that the products of chunk c - 1 read
+        const uint32_t idesc = instr_desc(TM, NT);
+        const uint32_t bytes = (uint32_t)(A_BYTES + NT * TK * 2);  // the two boxes (zero-filled parts count)
+        const int nchunks = (K + TK - 1) / TK;
+        unsigned ph_full[STAGES] = {0u, 0u, 0u}, ph_empty[STAGES] = {0u, 0u, 0u};
+        bool ok = true;
+        for (int c = 0; c < STAGES - 1 && c < nchunks; ++c) load_chunk(&tmA, &tmB, smem, full, c, m0, n0, bytes);
+        int waited_to = -1;  // the products of chunks up to this one are known to be done
+        for (int c = 0; c < nchunks && ok; ++c) {
+            const int st = c % STAGES;
+            ok = mbar_wait(&full[st], ph_full[st]);
+            ph_full[st] ^= 1u;
+            if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t sa = stage_a(c), sb = sa + A_BYTES;
+            const uint32_t sa = smem_u32(smem + st * STAGE_BYTES), sb = sa + A_BYTES;
             const int ksteps = min(TK, K - c * TK) / 16;
             for (int kk = 0; kk < ksteps; ++kk) {
-                // K = 16 per instruction: two core matrices along K, 256 bytes further on
-                const uint64_t da = smem_desc(sa + 256u * kk, 128u, SBO);
-                const uint64_t db = smem_desc(sb + 256u * kk, 128u, SBO);
+                // K = 16 per instruction: 32 bytes further along the 128-byte swizzle span
+                const uint64_t da = smem_desc_sw128(sa + 32u * kk);
+                const uint64_t db = smem_desc_sw128(sb + 32u * kk);
                 const uint32_t accum = (c > 0 || kk > 0) ? 1u : 0u;
                 asm volatile(
                     "{\n\t.reg .pred p;\n\t"
@@ -190,26 +188,36 @@ __global__ void __launch_bounds__(BT) k_gemm_tc(const __nv_bfloat16* __restrict_
                     : "memory");
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             smem_u32(&bar[c % STAGES]))
+                             smem_u32(&empty[st]))
                          : "memory");
+            const int cn = c + STAGES - 1;
+            if (cn < nchunks) {
+                if (cn >= STAGES) {
+                    // chunk cn - STAGES = c - 1 last read this stage
+                    const int so = (cn - STAGES) % STAGES;
+                    ok = mbar_wait(&empty[so], ph_empty[so]);
+                    ph_empty[so] ^= 1u;
+                    waited_to = cn - STAGES;
+                    if (!ok) break;
+                }
+                load_chunk(&tmA, &tmB, smem, full, cn, m0, n0, bytes);
+            }
         }
-    }
-    asm volatile("cp.async.wait_all;" ::: "memory");
-    if (!failed) {
-        // the commits of the last STAGES chunks, oldest first (the loop waited for every
-        // earlier one), so that no barrier still has an arrival pending when the CTA ends;
-        // the last covers every product
-        bool ok = true;
-        for (int c = max(0, nchunks - STAGES); c < nchunks; ++c) {
+        // the commits not waited for yet, oldest first: then every product is done and no
+        // barrier has an arrival pending when the CTA ends
+        for (int c = waited_to + 1; c < nchunks && ok; ++c) {
             const int st = c % STAGES;
-            ok = ok && mbar_wait(&bar[st], phase[st]);
-            phase[st] ^= 1u;
+            ok = mbar_wait(&empty[st], ph_empty[st]);
+            ph_empty[st] ^= 1u;
         }
-        if (__syncthreads_or(!ok)) failed = true;
+        if (!ok) {
+            s_fail = 1;
+            atomicOr(err, 2);
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     }
-    if (failed) {
-        if (threadIdx.x == 0) atomicOr(err, 2);
-    } else {
+    __syncthreads();
+    if (!s_fail) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         // the stages are free: warp w stages its 32 x 16 blocks in its own 2.5 KB
         float* stg = (float*)smem + warp * 32 * EPI_LD;
@@ -235,7 +243,8 @@ __global__ void __launch_bounds__(BT) k_gemm_tc(const __nv_bfloat16* __restrict_
             // lane = row of the block: four 16-byte writes into its staged row
 #pragma unroll
             for (int q = 0; q < 4; ++q)
-                *(float4*)(stg + lane * EPI_LD + 4 * q) = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+                *(float4*)(stg + lane * EPI_LD + 4 * q) =
+                    make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
             __syncwarp();
             // lanes l and l + 8k (k = 0..3) write the four 16-byte quarters of row l % 8 (+ 8 it)
 #pragma unroll
@@ -267,25 +276,69 @@ __global__ void __launch_bounds__(BT) k_gemm_tc(const __nv_bfloat16* __restrict_
 
 namespace od {
 
-// widest tile width (a multiple of 16, at most 256) that divides N
+// widest tile width (a multiple of 16, at most 128) that divides N
 int gemm_tc_tile(int N)
 {
-    for (int nt = 256; nt >= 16; nt -= 16)
+    for (int nt = tc::NT_MAX; nt >= 16; nt -= 16)
         if (N % nt == 0) return nt;
     return 0;
 }
+
+namespace {
+
+typedef CUresult (*EncodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encoder()
+{
+    static EncodeTiled fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiled)p;
+        cudaGetLastError();
+    });
+    return fn;
+}
+
+// a rows x K BF16 row-major matrix, read in boxes of box_rows x 64 with the 128-byte swizzle;
+// reads past the matrix return zeros
+bool encode(CUtensorMap* tm, const __nv_bfloat16* base, int rows, int K, int box_rows)
+{
+    const EncodeTiled fn = encoder();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)K * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)tc::TK, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)base, dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
 
 int launch_gemm_tc(const __nv_bfloat16* A, const __nv_bfloat16* B, const float* bias, float* C, __nv_bfloat16* Cb,
                    int M, int N, int K, int relu, int* err, cudaStream_t s)
 {
     const int nt = gemm_tc_tile(N);
     if (M < 1 || K < 16 || K % 16 || nt == 0) return (int)cudaErrorInvalidValue;
+    // TMA: 16-byte aligned bases (row strides are multiples of 16 bytes since K % 16 == 0)
+    if (((uintptr_t)A | (uintptr_t)B) & 15) return (int)cudaErrorMisalignedAddress;
+    alignas(64) CUtensorMap tmA, tmB;
+    if (!encode(&tmA, A, M, K, tc::TM) || !encode(&tmB, B, N, K, nt)) return (int)cudaErrorInvalidValue;
     // (per function and device: set on every call, it costs no device work)
     const cudaError_t e =
         cudaFuncSetAttribute(tc::k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES);
     if (e != cudaSuccess) return (int)e;
-    const dim3 grid((M + tc::TM - 1) / tc::TM, N / nt);
-    tc::k_gemm_tc<<<grid, tc::BT, tc::SMEM_BYTES, s>>>(A, B, bias, C, Cb, M, N, K, nt, relu, err);
+    const dim3 grid(N / nt, (M + tc::TM - 1) / tc::TM);
+    if (grid.y > 65535u) return (int)cudaErrorInvalidValue;
+    tc::k_gemm_tc<<<grid, tc::BT, tc::SMEM_BYTES, s>>>(tmA, tmB, bias, C, Cb, M, N, K, nt, relu, err);
     return (int)cudaGetLastError();
 }
 
