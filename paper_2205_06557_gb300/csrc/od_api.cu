@@ -389,9 +389,14 @@ void derive(const od_params* p, Phys& P, od_handle* h)
     h->qscale = (float)std::ldexp(1.0, K);
     // close-pair correction: pairs nearer than d_c = 0.005 max(1, |s|max / 4) scaled units
     // (the FP32 rounding of |s| moves them most relative to their separation; what it
-    // leaves in the farther pairs grows like |s|max / d_c); hashed cells 2.1 d_c wide
+    // leaves in the farther pairs grows like |s|max / d_c); hashed cells 2.1 d_c wide.
+    // d_c is held to half a neighbour per ion at the mean density, 4/3 pi d_c^3 n_s <= 1/2:
+    // in domains far longer than the Debye length (|s|max > 10) the rule would put hundreds
+    // of ions within d_c of each ion and the walk of its cells would cost more than the
+    // pair forces; there the FP32 coordinates bound the per-ion accuracy instead
     const double smax = std::sqrt(Rs * Rs + Hs * Hs);
-    const double dc = 0.005 * std::max(1.0, 0.25 * smax);
+    const double dc_cap = std::cbrt(0.375 / (kPI * std::max(n_s, 1e-300)));
+    const double dc = std::min(0.005 * std::max(1.0, 0.25 * smax), dc_cap);
     P.cp_dc2 = dc * dc;
     P.cp_hinv = (float)(1.0 / (2.1 * dc));
     P.cp_on = !(p->flags & (OD_F_NO_IONION | OD_F_FP64_PAIRS));

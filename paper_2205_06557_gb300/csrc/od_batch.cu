@@ -91,8 +91,8 @@ __global__ void __launch_bounds__(BATCH_BT, 65536 / (BATCH_BT * 128))
                 forces_unit<BATCH_BT, IPT>(d.B.fpos, d.B.part, d.F, tk.y / d.F.JS, tk.y % d.F.JS, sj);
             }
             break;
-        case 2: kick_body<BATCH_BT>(d.P, d.B, d.F, tune ? 1 : 0, tk.y); break;
-        default: dust_body(d.P, d.B, d.nK, 0); break;
+        case 2: kick_body<BATCH_BT, 1>(d.P, d.B, d.F, tune ? 1 : 0, tk.y); break;
+        default: dust_body<false>(d.P, d.B, d.nK, 0); break;
         }
         // publish completion of this task to the run's phase counter
         __threadfence();

@@ -278,12 +278,17 @@ __device__ __forceinline__ void close_pair_term(float4 fi, float4 fj, double ex,
     t = make_float3(fmaf(c, fx, proj * qx), fmaf(c, fy, proj * qy), fmaf(c, fz, proj * qz));
 }
 
-template <class PosF>
+// WIDE lists (a divisor of 8) are walked side by side at a time: 8 for latency (a run of a
+// few thousand ions, where each walk step is a memory round trip on the step's critical
+// path), 1 where registers are scarce (the batched kernel, held to 128 per thread, whose
+// pair tasks would otherwise spill).
+template <int WIDE = 8, class PosF>
 __device__ void close_pair_corr(const unsigned long long* __restrict__ head, const int* __restrict__ next,
                                 const float4* __restrict__ fpos, unsigned mask, float hinv, double dc2,
                                 unsigned epoch, int n_live, double ls_inv, int i, double xi, double yi, double zi,
                                 PosF pos, double& cx, double& cy, double& cz)
 {
+    static_assert(WIDE >= 1 && 8 % WIDE == 0, "the eight lists split into equal groups");
     const float4 fi = fpos[i];
     // lower corner of the 2 x 2 x 2 cells around the ion: towards the nearer cell face
     const float ux = fi.x * hinv, uy = fi.y * hinv, uz = fi.z * hinv;
@@ -298,48 +303,54 @@ __device__ void close_pair_corr(const unsigned long long* __restrict__ head, con
     cx = cy = cz = 0.0;
     int last = -1;  // with more than CP_KEEP candidates: the pairs up to j = last are summed
     for (int round = 0; round < n_live; ++round) {
-        // the eight lists are walked side by side: each step loads the next entry (position
-        // and link) of every list at once, so a walk costs one memory round trip per list
-        // level, not one per entry.  Candidates: another ion of the same cell, j > last,
-        // within the correction distance by the FP32 pre-test (a 1% margin in d^2 covers
-        // its rounding); the CP_KEEP smallest j are kept.
-        int jc[8];
-#pragma unroll
-        for (int c = 0; c < 8; ++c) jc[c] = (unsigned)(hws[c] >> 32) == epoch ? (int)(unsigned)hws[c] : -1;
+        // WIDE lists at a time are walked side by side: each step loads the next entry
+        // (position and link) of every one of them at once, so a walk costs one memory round
+        // trip per list level, not one per entry.  Candidates: another ion of the same cell,
+        // j > last, within the correction distance by the FP32 pre-test (a 1% margin in d^2
+        // covers its rounding); the CP_KEEP smallest j are kept.
         int cand[CP_KEEP];
         int nc = 0, over = 0;
-        for (int level = 0; level < n_live; ++level) {
-            float4 fj[8];
-            int nx[8];
-            bool any = false;
 #pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                nx[c] = -1;
-                if (jc[c] >= 0 && jc[c] < n_live) {
-                    fj[c] = fpos[jc[c]];
-                    nx[c] = next[jc[c]];
-                    any = true;
-                }
+        for (int g = 0; g < 8; g += WIDE) {
+            int jc[WIDE];
+#pragma unroll
+            for (int w = 0; w < WIDE; ++w) {
+                const unsigned long long hw = hws[g + w];
+                jc[w] = (unsigned)(hw >> 32) == epoch ? (int)(unsigned)hw : -1;
             }
-            if (!any) break;
+            for (int level = 0; level < n_live; ++level) {
+                float4 fj[WIDE];
+                int nx[WIDE];
+                bool any = false;
 #pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                const int j = jc[c];
-                jc[c] = nx[c];
-                if (!(j >= 0 && j < n_live) || j == i || j <= last) continue;
-                if (cp_cell(fj[c].x, hinv) != lx + (c & 1) || cp_cell(fj[c].y, hinv) != ly + ((c >> 1) & 1) ||
-                    cp_cell(fj[c].z, hinv) != lz + (c >> 2))
-                    continue;  // another cell sharing the bucket
-                const float gx = fj[c].x - fi.x, gy = fj[c].y - fi.y, gz = fj[c].z - fi.z;
-                if (fmaf(gx, gx, fmaf(gy, gy, gz * gz)) > dc2_f) continue;
-                if (nc < CP_KEEP) {
-                    cand[nc++] = j;
-                } else {
-                    // keep the CP_KEEP smallest j; the rest wait for the next round
-                    over = 1;
-                    int m = 0;
-                    for (int k = 1; k < CP_KEEP; ++k) m = cand[k] > cand[m] ? k : m;
-                    if (j < cand[m]) cand[m] = j;
+                for (int w = 0; w < WIDE; ++w) {
+                    nx[w] = -1;
+                    if (jc[w] >= 0 && jc[w] < n_live) {
+                        fj[w] = fpos[jc[w]];
+                        nx[w] = next[jc[w]];
+                        any = true;
+                    }
+                }
+                if (!any) break;
+#pragma unroll
+                for (int w = 0; w < WIDE; ++w) {
+                    const int j = jc[w], c = g + w;
+                    jc[w] = nx[w];
+                    if (!(j >= 0 && j < n_live) || j == i || j <= last) continue;
+                    if (cp_cell(fj[w].x, hinv) != lx + (c & 1) || cp_cell(fj[w].y, hinv) != ly + ((c >> 1) & 1) ||
+                        cp_cell(fj[w].z, hinv) != lz + (c >> 2))
+                        continue;  // another cell sharing the bucket
+                    const float gx = fj[w].x - fi.x, gy = fj[w].y - fi.y, gz = fj[w].z - fi.z;
+                    if (fmaf(gx, gx, fmaf(gy, gy, gz * gz)) > dc2_f) continue;
+                    if (nc < CP_KEEP) {
+                        cand[nc++] = j;
+                    } else {
+                        // keep the CP_KEEP smallest j; the rest wait for the next round
+                        over = 1;
+                        int m = 0;
+                        for (int k = 1; k < CP_KEEP; ++k) m = cand[k] > cand[m] ? k : m;
+                        if (j < cand[m]) cand[m] = j;
+                    }
                 }
             }
         }
@@ -689,7 +700,7 @@ __device__ __forceinline__ double warp_sum(double v)
 
 // mode 0: after the push (second half kick + collisions); mode 1: forces only (creation
 // or a replaced ion state)
-template <int BT>
+template <int BT, int CP_WIDE = 8>
 __device__ __forceinline__ void kick_body(const Phys& P, const Bufs& B, const ForceArgs& F, int mode, int blk)
 {
     __shared__ double s_red[BT / 32][3];
@@ -785,14 +796,14 @@ __device__ __forceinline__ void kick_body(const Phys& P, const Bufs& B, const Fo
             if (P.cp_on) {
                 const double* Xb = B.x[buf];
                 double cx, cy, cz;
-                close_pair_corr(B.cp_head, B.cp_next, B.fpos, P.cp_mask, P.cp_hinv, P.cp_dc2, C->cp_epoch, C->n_cur,
-                                P.ls_inv, i, x, y, z,
-                                [&](int j, double& xj, double& yj, double& zj) {
-                                    xj = Xb[j];
-                                    yj = Xb[cap + j];
-                                    zj = Xb[2 * cap + j];
-                                },
-                                cx, cy, cz);
+                close_pair_corr<CP_WIDE>(B.cp_head, B.cp_next, B.fpos, P.cp_mask, P.cp_hinv, P.cp_dc2, C->cp_epoch,
+                                         C->n_cur, P.ls_inv, i, x, y, z,
+                                         [&](int j, double& xj, double& yj, double& zj) {
+                                             xj = Xb[j];
+                                             yj = Xb[cap + j];
+                                             zj = Xb[2 * cap + j];
+                                         },
+                                         cx, cy, cz);
                 px += cx;
                 py += cy;
                 pz += cz;
@@ -909,6 +920,10 @@ __device__ __forceinline__ void kick_body(const Phys& P, const Bufs& B, const Fo
 // --------------------------------------------------------------- grain tail
 constexpr int DUST_BT = 256;
 
+// HOIST_WSUM: the grains' window sums are loaded with the other control values (one memory
+// round trip fewer in a small run's step); the batched kernel, held to 128 registers, reads
+// them where they are added instead
+template <bool HOIST_WSUM = true>
 __device__ __forceinline__ void dust_body(const Phys& P, const Bufs& B, int nb, int mode)
 {
     __shared__ double s_S[MAXD][3];
@@ -934,7 +949,7 @@ __device__ __forceinline__ void dust_body(const Phys& P, const Bufs& B, int nb, 
         egx = C->eg[k][0];
         egy = C->eg[k][1];
         egz = C->eg[k][2];
-        if (mode == 0)
+        if (HOIST_WSUM && mode == 0)
 #pragma unroll
             for (int t = 0; t < REC; ++t) wk[t] = C->wsum[k][t];
     }
@@ -1023,7 +1038,7 @@ __device__ __forceinline__ void dust_body(const Phys& P, const Bufs& B, int nb, 
                 for (int t = 0; t < REC; ++t) o[t] = s_rec[k][t];
             }
             if (step + 1 >= P.avg_start)
-                for (int t = 0; t < REC; ++t) C->wsum[k][t] = wk[t] + s_rec[k][t];
+                for (int t = 0; t < REC; ++t) C->wsum[k][t] = (HOIST_WSUM ? wk[t] : C->wsum[k][t]) + s_rec[k][t];
         }
     }
     if (mode != 0) return;
