@@ -14,9 +14,9 @@
 // descriptors name (SWIZZLE_128B, 1,024 bytes between 8-row groups, K steps of 32 bytes
 // within the swizzle span); rows past M and columns past K are zero-filled by the loads.
 // After the last chunk the four warps read the accumulator with tcgen05.ld (warp w: rows
-// 32w .. 32w + 31, 16 columns at a time), add the bias, apply the relu and stage each
-// 32 x 16 block in shared memory, so that the stores of C and of its BF16 copy write 64
-// contiguous bytes of a row per four lanes.
+// 32w .. 32w + 31, 32 columns at a time), add the bias, apply the relu and stage each
+// 32 x 32 block in shared memory, so that the stores of C and of its BF16 copy write 128
+// contiguous bytes of a row per eight lanes.
 //
 // Every wait on an mbarrier is bounded: a wait that runs out sets bit 1 of *err, stops
 // the CTA's further products and still frees its tensor memory before returning.
@@ -42,7 +42,7 @@ constexpr int B_BYTES = NT_MAX * TK * 2;   // 16 KB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr uint32_t SBO = 8 * TK * 2;       // bytes between 8-row groups (1,024)
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 128;  // stages, alignment, barriers
-constexpr int EPI_LD = 20;                 // staged epilogue row stride (floats; 80 B)
+constexpr int EPI_LD = 36;                 // staged epilogue row stride (floats; 144 B)
 constexpr long long WAIT_LIMIT = 1ll << 22;  // polls of an mbarrier before giving up
 static_assert(A_BYTES % 1024 == 0 && B_BYTES % 1024 == 0, "swizzled tiles start on 1,024-byte boundaries");
 static_assert(4 * 32 * EPI_LD * 4 <= STAGES * STAGE_BYTES, "epilogue staging fits the stages");
@@ -119,6 +119,99 @@ __device__ __forceinline__ void load_chunk(const CUtensorMap* tmA, const CUtenso
         : "memory");
 }
 
+// tcgen05.ld of W = 16 or 32 consecutive accumulator columns of the warp's 32 lanes (rows),
+// issued without waiting; tmem_wait(v) waits for every load the thread issued and names v as
+// its operands, so that no use of v moves before it
+template <int W>
+__device__ __forceinline__ void tmem_issue(uint32_t taddr, uint32_t (&v)[W]);
+
+template <>
+__device__ __forceinline__ void tmem_issue<16>(uint32_t taddr, uint32_t (&v)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+          "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr));
+}
+
+template <>
+__device__ __forceinline__ void tmem_issue<32>(uint32_t taddr, uint32_t (&v)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+          "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
+          "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+          "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr));
+}
+
+template <int W>
+__device__ __forceinline__ void tmem_wait(uint32_t (&v)[W])
+{
+#pragma unroll
+    for (int e = 0; e < W; e += 16)
+        asm volatile("" : "+r"(v[e]), "+r"(v[e + 1]), "+r"(v[e + 2]), "+r"(v[e + 3]), "+r"(v[e + 4]), "+r"(v[e + 5]),
+                     "+r"(v[e + 6]), "+r"(v[e + 7]), "+r"(v[e + 8]), "+r"(v[e + 9]), "+r"(v[e + 10]), "+r"(v[e + 11]),
+                     "+r"(v[e + 12]), "+r"(v[e + 13]), "+r"(v[e + 14]), "+r"(v[e + 15])::"memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int e = 0; e < W; e += 16)
+        asm volatile("" : "+r"(v[e]), "+r"(v[e + 1]), "+r"(v[e + 2]), "+r"(v[e + 3]), "+r"(v[e + 4]), "+r"(v[e + 5]),
+                     "+r"(v[e + 6]), "+r"(v[e + 7]), "+r"(v[e + 8]), "+r"(v[e + 9]), "+r"(v[e + 10]), "+r"(v[e + 11]),
+                     "+r"(v[e + 12]), "+r"(v[e + 13]), "+r"(v[e + 14]), "+r"(v[e + 15])::"memory");
+}
+
+// One 32 x W block of the warp's rows (W = 16 or 32 columns from column col of C): bias, relu,
+// then staged in shared memory (lane = row, W/4 16-byte writes; rows EPI_LD floats apart, so
+// each 8-lane phase hits distinct banks) and stored with W/4 lanes per row, 128 (W = 32) or 64
+// (W = 16) contiguous bytes of a row per instruction's row.
+template <int W>
+__device__ __forceinline__ void epilogue_block(const uint32_t (&v)[W], float* stg, int lane, int rb, int M, int N,
+                                               int col, const float* __restrict__ bias, int relu,
+                                               float* __restrict__ C, __nv_bfloat16* __restrict__ Cb)
+{
+    constexpr int QR = W / 4;     // 16-byte pieces per row
+    constexpr int RPI = 32 / QR;  // rows per store instruction
+    float o[W];
+#pragma unroll
+    for (int q = 0; q < QR; ++q) {
+        // the bias in 16-byte loads (col is a multiple of 16, the bias 16-byte aligned)
+        const float4 b4 = bias ? __ldg((const float4*)(bias + col) + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float bq[4] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            float x = __uint_as_float(v[4 * q + e]) + bq[e];
+            if (relu) x = fmaxf(x, 0.f);
+            o[4 * q + e] = x;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < QR; ++q)
+        *(float4*)(stg + lane * EPI_LD + 4 * q) = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+    __syncwarp();
+#pragma unroll
+    for (int it = 0; it < QR; ++it) {
+        // W = 32: lanes 8k .. 8k + 7 write row 4 it + k; W = 16: lanes l, l + 8, l + 16, l + 24
+        // write the four pieces of row 8 it + l % 8
+        const int r = W == 32 ? it * RPI + (lane >> 3) : it * RPI + (lane & 7);
+        const int q = W == 32 ? (lane & 7) : (lane >> 3);
+        const float4 x = *(const float4*)(stg + r * EPI_LD + 4 * q);
+        if (rb + r < M) {
+            const long long off = (long long)(rb + r) * N + col + 4 * q;
+            *(float4*)(C + off) = x;
+            if (Cb) {
+                __nv_bfloat162 h[2] = {__floats2bfloat162_rn(x.x, x.y), __floats2bfloat162_rn(x.z, x.w)};
+                *(uint2*)(Cb + off) = *(const uint2*)h;
+            }
+        }
+    }
+    __syncwarp();
+}
+
 __global__ void __launch_bounds__(BT) k_gemm_tc(const __grid_constant__ CUtensorMap tmA,
                                                 const __grid_constant__ CUtensorMap tmB, const float* __restrict__ bias,
                                                 float* __restrict__ C, __nv_bfloat16* __restrict__ Cb, int M, int N,
@@ -163,7 +256,7 @@ __global__ void __launch_bounds__(BT) k_gemm_tc(const __grid_constant__ CUtensor
         const uint32_t idesc = instr_desc(TM, NT);
         const uint32_t bytes = (uint32_t)(A_BYTES + NT * TK * 2);  // the two boxes (zero-filled parts count)
         const int nchunks = (K + TK - 1) / TK;
-        unsigned ph_full[STAGES] = {0u, 0u, 0u}, ph_empty[STAGES] = {0u, 0u, 0u};
+        unsigned ph_full[STAGES] = {}, ph_empty[STAGES] = {};
         bool ok = true;
         for (int c = 0; c < STAGES - 1 && c < nchunks; ++c) load_chunk(&tmA, &tmB, smem, full, c, m0, n0, bytes);
         int waited_to = -1;  // the products of chunks up to this one are known to be done
@@ -219,48 +312,31 @@ __global__ void __launch_bounds__(BT) k_gemm_tc(const __grid_constant__ CUtensor
     __syncthreads();
     if (!s_fail) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // the stages are free: warp w stages its 32 x 16 blocks in its own 2.5 KB
+        // the stages are free: warp w stages its blocks in its own 4.5 KB
         float* stg = (float*)smem + warp * 32 * EPI_LD;
         const int rb = m0 + warp * 32;  // the warp's first row
-        for (int c0 = 0; c0 < NT; c0 += 16) {
-            uint32_t v[16];
-            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-                "%14, %15}, [%16];"
-                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-                : "r"(taddr));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            float o[16];
-#pragma unroll
-            for (int e = 0; e < 16; ++e) {
-                float x = __uint_as_float(v[e]);
-                if (bias) x += __ldg(bias + n0 + c0 + e);
-                if (relu) x = fmaxf(x, 0.f);
-                o[e] = x;
+        const uint32_t tw = tmem + ((uint32_t)(warp * 32) << 16);
+        const int n32 = NT / 32;
+        if (n32 > 0) {
+            // the next block's columns are read from tensor memory while this block is stored
+            uint32_t va[32], vb[32];
+            tmem_issue<32>(tw, va);
+            tmem_wait<32>(va);
+            for (int b = 0; b < n32; b += 2) {
+                if (b + 1 < n32) tmem_issue<32>(tw + (uint32_t)(32 * (b + 1)), vb);
+                epilogue_block<32>(va, stg, lane, rb, M, N, n0 + 32 * b, bias, relu, C, Cb);
+                if (b + 1 >= n32) break;
+                tmem_wait<32>(vb);
+                if (b + 2 < n32) tmem_issue<32>(tw + (uint32_t)(32 * (b + 2)), va);
+                epilogue_block<32>(vb, stg, lane, rb, M, N, n0 + 32 * (b + 1), bias, relu, C, Cb);
+                if (b + 2 < n32) tmem_wait<32>(va);
             }
-            // lane = row of the block: four 16-byte writes into its staged row
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-                *(float4*)(stg + lane * EPI_LD + 4 * q) =
-                    make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
-            __syncwarp();
-            // lanes l and l + 8k (k = 0..3) write the four 16-byte quarters of row l % 8 (+ 8 it)
-#pragma unroll
-            for (int it = 0; it < 4; ++it) {
-                const int r = it * 8 + (lane & 7), q = lane >> 3;
-                const float4 x = *(const float4*)(stg + r * EPI_LD + 4 * q);
-                if (rb + r < M) {
-                    const long long off = (long long)(rb + r) * N + n0 + c0 + 4 * q;
-                    *(float4*)(C + off) = x;
-                    if (Cb) {
-                        __nv_bfloat162 h[2] = {__floats2bfloat162_rn(x.x, x.y), __floats2bfloat162_rn(x.z, x.w)};
-                        *(uint2*)(Cb + off) = *(const uint2*)h;
-                    }
-                }
-            }
-            __syncwarp();
+        }
+        if (NT % 32) {
+            uint32_t v16[16];
+            tmem_issue<16>(tw + (uint32_t)(32 * n32), v16);
+            tmem_wait<16>(v16);
+            epilogue_block<16>(v16, stg, lane, rb, M, N, n0 + 32 * n32, bias, relu, C, Cb);
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
