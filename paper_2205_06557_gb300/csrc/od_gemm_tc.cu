@@ -404,8 +404,10 @@ int launch_gemm_tc(const __nv_bfloat16* A, const __nv_bfloat16* B, const float* 
 {
     const int nt = gemm_tc_tile(N);
     if (M < 1 || K < 16 || K % 16 || nt == 0) return (int)cudaErrorInvalidValue;
-    // TMA: 16-byte aligned bases (row strides are multiples of 16 bytes since K % 16 == 0)
-    if (((uintptr_t)A | (uintptr_t)B) & 15) return (int)cudaErrorMisalignedAddress;
+    // TMA: 16-byte aligned bases (row strides are multiples of 16 bytes since K % 16 == 0);
+    // the epilogue's 16-byte stores and bias loads: 16-byte aligned C, Cb and bias
+    if (((uintptr_t)A | (uintptr_t)B | (uintptr_t)C | (uintptr_t)Cb | (uintptr_t)bias) & 15)
+        return (int)cudaErrorMisalignedAddress;
     alignas(64) CUtensorMap tmA, tmB;
     if (!encode(&tmA, A, M, K, tc::TM) || !encode(&tmB, B, N, K, nt)) return (int)cudaErrorInvalidValue;
     // (per function and device: set on every call, it costs no device work)
